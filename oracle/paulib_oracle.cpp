@@ -1,0 +1,338 @@
+// paulib_oracle.cpp -- TEST INFRASTRUCTURE ONLY.
+//
+// A plain, slow, obviously-correct CPU definition of the Pauli-sum product and
+// its canonical form.  It exists so the tests, the smoke check and the CPU
+// baseline leg of the benchmark have something independent to compare the GPU
+// library against.  Nothing in the product library links, includes or calls
+// this file, and this file shares no code with the library.
+//
+// What it computes (PauLIB, Sec. III):
+//   * Single-qubit products come from the paper's table of Pauli products
+//     (Sec. III-A): I is neutral, P*P = I, and
+//       XY = iZ, YZ = iX, ZX = iY,   YX = -iZ, ZY = -iX, XZ = -iY.
+//   * A Pauli string product is taken qubit by qubit with that table and the
+//     phases are accumulated into one global phase i^k (Sec. III-A, the worked
+//     example (XIZ)(ZIX) = YIY).
+//   * Qubit letters are decoded from the binary symplectic (x|z) bits of
+//     Table I: I=(0,0), Z=(0,1), X=(1,0), Y=(1,1).  Qubit q lives in word q/64
+//     (Sec. III-F), bit q%64 (least significant bit = lowest qubit; the paper
+//     fixes only the word index, this bit order is our reading).
+//   * A Pauli sum is sum_j c_j P_j with complex c_j (Eq. 2).
+//   * The product of two sums is the outer product: every left term times
+//     every right term (Sec. IV-B/IV-C).  Raw order: the block of right term j
+//     holds the products of all left terms i, i.e. raw index j*|A| + i.
+//   * Canonical form = sort by a lexicographic key of the packed words and
+//     merge adjacent duplicates by adding coefficients (Sec. III-G).  The key
+//     is (x_0..x_{W-1}, z_0..z_{W-1}) compared as unsigned 64-bit words, word
+//     0 most significant (our reading: the paper names a lexicographic key over
+//     the packed words without fixing the word order).  Terms whose merged
+//     coefficient is zero are kept (the paper drops terms only in truncation).
+//
+// Arithmetic: FP64 throughout, built with -ffp-contract=off.  Duplicate
+// coefficients are summed with Neumaier's compensated summation so the oracle's
+// own rounding error stays far below the tolerance the GPU path is held to.
+// Every merged key also reports sum |c_a||c_b| over its contributions and the
+// contribution count, which the tolerance and the tests use.
+//
+// Data layout at this interface: struct of arrays as in the paper's PauliSumSoA
+// (Sec. IV-A): word w of term t at x[w*n_terms + t]; complex coefficients are
+// interleaved (re, im); optional per-term phase exponents k in {0,1,2,3} mean
+// the term is i^k * c * P.
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <cmath>
+#include <map>
+#include <vector>
+
+namespace {
+
+enum Letter { I_ = 0, X_ = 1, Y_ = 2, Z_ = 3 };
+
+struct Prod { int letter; int k; };
+
+// The paper's single-qubit multiplication table (Sec. III-A), written out
+// entry by entry.  k is the exponent of i in the phase.
+Prod letter_product(int a, int b) {
+    if (a == I_) return {b, 0};
+    if (b == I_) return {a, 0};
+    if (a == b) return {I_, 0};
+    if (a == X_ && b == Y_) return {Z_, 1};   // XY =  iZ
+    if (a == Y_ && b == Z_) return {X_, 1};   // YZ =  iX
+    if (a == Z_ && b == X_) return {Y_, 1};   // ZX =  iY
+    if (a == Y_ && b == X_) return {Z_, 3};   // YX = -iZ
+    if (a == Z_ && b == Y_) return {X_, 3};   // ZY = -iX
+    if (a == X_ && b == Z_) return {Y_, 3};   // XZ = -iY
+    std::abort();
+}
+
+// Table I: (x-bit, z-bit) -> letter.
+int decode(int xbit, int zbit) {
+    if (!xbit && !zbit) return I_;
+    if (!xbit && zbit) return Z_;
+    if (xbit && !zbit) return X_;
+    return Y_;
+}
+void encode(int letter, int* xbit, int* zbit) {
+    *xbit = (letter == X_ || letter == Y_) ? 1 : 0;
+    *zbit = (letter == Z_ || letter == Y_) ? 1 : 0;
+}
+
+int words_for(int n) { return (n + 63) / 64; }
+
+int get_bit(const uint64_t* w, int q) { return (int)((w[q / 64] >> (q % 64)) & 1ull); }
+void set_bit(uint64_t* w, int q) { w[q / 64] |= (1ull << (q % 64)); }
+
+// One Pauli string held as per-word arrays of length W.
+struct Str { std::vector<uint64_t> x, z; };
+
+Str load_term(int W, int64_t n_terms, const uint64_t* xs, const uint64_t* zs, int64_t t) {
+    Str s; s.x.assign(W, 0); s.z.assign(W, 0);
+    for (int w = 0; w < W; ++w) { s.x[w] = xs[(int64_t)w * n_terms + t]; s.z[w] = zs[(int64_t)w * n_terms + t]; }
+    return s;
+}
+
+// Product of two strings, qubit by qubit (Sec. III-A): returns k with
+// P_a P_b = i^k P_out.
+int string_product(int n, const Str& a, const Str& b, Str* out) {
+    int W = words_for(n);
+    out->x.assign(W, 0); out->z.assign(W, 0);
+    int k = 0;
+    for (int q = 0; q < n; ++q) {
+        int la = decode(get_bit(a.x.data(), q), get_bit(a.z.data(), q));
+        int lb = decode(get_bit(b.x.data(), q), get_bit(b.z.data(), q));
+        Prod p = letter_product(la, lb);
+        k = (k + p.k) % 4;
+        int xb, zb; encode(p.letter, &xb, &zb);
+        if (xb) set_bit(out->x.data(), q);
+        if (zb) set_bit(out->z.data(), q);
+    }
+    return k;
+}
+
+// Key = (x_0..x_{W-1}, z_0..z_{W-1}); std::vector's operator< is the
+// lexicographic comparison with unsigned 64-bit elements.
+std::vector<uint64_t> key_of(const Str& s) {
+    std::vector<uint64_t> k(s.x);
+    k.insert(k.end(), s.z.begin(), s.z.end());
+    return k;
+}
+
+struct Cplx { double re, im; };
+
+Cplx cmul(Cplx a, Cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+
+// Multiply by i^k exactly (a swap and/or sign flips, no rounding).
+Cplx rot(Cplx c, int k) {
+    switch (k & 3) {
+        case 0: return c;
+        case 1: return {-c.im, c.re};
+        case 2: return {-c.re, -c.im};
+        default: return {c.im, -c.re};
+    }
+}
+
+// Neumaier's compensated sum (improved Kahan-Babuska).
+struct Neumaier {
+    double s = 0.0, c = 0.0;
+    void add(double v) {
+        double t = s + v;
+        if (std::fabs(s) >= std::fabs(v)) c += (s - t) + v; else c += (v - t) + s;
+        s = t;
+    }
+    double value() const { return s + c; }
+};
+
+struct Acc { Neumaier re, im; double abs_sum = 0.0; int64_t count = 0; };
+
+struct Result {
+    int n = 0, W = 0;
+    std::vector<std::vector<uint64_t>> keys;
+    std::vector<double> coef;      // interleaved re, im
+    std::vector<double> abs_sum;
+    std::vector<int64_t> count;
+};
+
+void emit(const std::map<std::vector<uint64_t>, Acc>& m, Result* r) {
+    for (const auto& kv : m) {
+        r->keys.push_back(kv.first);
+        r->coef.push_back(kv.second.re.value());
+        r->coef.push_back(kv.second.im.value());
+        r->abs_sum.push_back(kv.second.abs_sum);
+        r->count.push_back(kv.second.count);
+    }
+}
+
+Cplx load_coef(const double* c, int64_t t) { return {c[2 * t], c[2 * t + 1]}; }
+
+}  // namespace
+
+extern "C" {
+
+int oracle_abi_version(void) { return 1; }
+
+// Single-qubit product; letters 0=I, 1=X, 2=Y, 3=Z.
+void oracle_letter_product(int a, int b, int* out_letter, int* out_k) {
+    Prod p = letter_product(a, b);
+    *out_letter = p.letter; *out_k = p.k;
+}
+
+// Product of two single strings given as W-word arrays; writes the product
+// string and returns k (P_a P_b = i^k P_out).
+int oracle_string_product(int n, const uint64_t* xa, const uint64_t* za, const uint64_t* xb,
+                          const uint64_t* zb, uint64_t* xo, uint64_t* zo) {
+    int W = words_for(n);
+    Str a, b, o;
+    a.x.assign(xa, xa + W); a.z.assign(za, za + W);
+    b.x.assign(xb, xb + W); b.z.assign(zb, zb + W);
+    int k = string_product(n, a, b, &o);
+    for (int w = 0; w < W; ++w) { xo[w] = o.x[w]; zo[w] = o.z[w]; }
+    return k;
+}
+
+// Raw outer product (Sec. IV-C): output slot j*na + i holds a_i * b_j with
+// key a_i XOR b_j, phase k = k_a + k_b + k_pair (mod 4) and the unrotated
+// coefficient c_a * c_b.  ka/kb may be NULL (all zero).  Output is SoA with
+// n_out = na*nb terms.
+void oracle_multiply_raw(int n, int64_t na, const uint64_t* ax, const uint64_t* az, const double* ac,
+                         const uint8_t* ka, int64_t nb, const uint64_t* bx, const uint64_t* bz,
+                         const double* bc, const uint8_t* kb, uint64_t* ox, uint64_t* oz, double* oc,
+                         uint8_t* ok) {
+    int W = words_for(n);
+    int64_t nout = na * nb;
+    for (int64_t j = 0; j < nb; ++j) {
+        Str b = load_term(W, nb, bx, bz, j);
+        for (int64_t i = 0; i < na; ++i) {
+            Str a = load_term(W, na, ax, az, i);
+            Str o;
+            int k = string_product(n, a, b, &o);
+            k = (k + (ka ? ka[i] : 0) + (kb ? kb[j] : 0)) % 4;
+            int64_t t = j * na + i;
+            for (int w = 0; w < W; ++w) { ox[(int64_t)w * nout + t] = o.x[w]; oz[(int64_t)w * nout + t] = o.z[w]; }
+            Cplx c = cmul(load_coef(ac, i), load_coef(bc, j));
+            oc[2 * t] = c.re; oc[2 * t + 1] = c.im;
+            ok[t] = (uint8_t)k;
+        }
+    }
+}
+
+// Canonical product: C = sum_i sum_j c_a_i c_b_j (P_a_i P_b_j), one term per
+// distinct product string, in ascending key order.  Returns an opaque handle.
+void* oracle_multiply_canonical(int n, int64_t na, const uint64_t* ax, const uint64_t* az,
+                                const double* ac, const uint8_t* ka, int64_t nb, const uint64_t* bx,
+                                const uint64_t* bz, const double* bc, const uint8_t* kb) {
+    int W = words_for(n);
+    std::map<std::vector<uint64_t>, Acc> m;
+    for (int64_t j = 0; j < nb; ++j) {
+        Str b = load_term(W, nb, bx, bz, j);
+        Cplx cb = load_coef(bc, j);
+        for (int64_t i = 0; i < na; ++i) {
+            Str a = load_term(W, na, ax, az, i);
+            Str o;
+            int k = string_product(n, a, b, &o);
+            k = (k + (ka ? ka[i] : 0) + (kb ? kb[j] : 0)) % 4;
+            Cplx ca = load_coef(ac, i);
+            Cplx c = rot(cmul(ca, cb), k);
+            Acc& acc = m[key_of(o)];
+            acc.re.add(c.re); acc.im.add(c.im);
+            acc.abs_sum += std::hypot(ca.re, ca.im) * std::hypot(cb.re, cb.im);
+            acc.count += 1;
+        }
+    }
+    Result* r = new Result; r->n = n; r->W = W;
+    emit(m, r);
+    return r;
+}
+
+// Canonical form of one sum (sort by key, merge duplicates); a term with phase
+// k contributes i^k c.  kin may be NULL.
+void* oracle_compress(int n, int64_t nt, const uint64_t* xs, const uint64_t* zs, const double* cs,
+                      const uint8_t* kin) {
+    int W = words_for(n);
+    std::map<std::vector<uint64_t>, Acc> m;
+    for (int64_t t = 0; t < nt; ++t) {
+        Str s = load_term(W, nt, xs, zs, t);
+        Cplx c0 = load_coef(cs, t);
+        Cplx c = rot(c0, kin ? kin[t] : 0);
+        Acc& acc = m[key_of(s)];
+        acc.re.add(c.re); acc.im.add(c.im);
+        acc.abs_sum += std::hypot(c0.re, c0.im);
+        acc.count += 1;
+    }
+    Result* r = new Result; r->n = n; r->W = W;
+    emit(m, r);
+    return r;
+}
+
+int64_t oracle_result_size(const void* h) { return (int64_t)static_cast<const Result*>(h)->keys.size(); }
+
+// Copies a result out as SoA words, interleaved coefficients, per-term
+// sum |contribution| and contribution counts (any output pointer may be NULL).
+void oracle_result_copy(const void* h, uint64_t* ox, uint64_t* oz, double* oc, double* oabs,
+                        int64_t* ocount) {
+    const Result* r = static_cast<const Result*>(h);
+    int64_t u = (int64_t)r->keys.size();
+    for (int64_t t = 0; t < u; ++t) {
+        for (int w = 0; w < r->W; ++w) {
+            if (ox) ox[(int64_t)w * u + t] = r->keys[t][w];
+            if (oz) oz[(int64_t)w * u + t] = r->keys[t][r->W + w];
+        }
+        if (oc) { oc[2 * t] = r->coef[2 * t]; oc[2 * t + 1] = r->coef[2 * t + 1]; }
+        if (oabs) oabs[t] = r->abs_sum[t];
+        if (ocount) ocount[t] = r->count[t];
+    }
+}
+
+void oracle_result_free(void* h) { delete static_cast<Result*>(h); }
+
+// Coefficient of given product strings in A*B, one query at a time, straight
+// from the definition: every pair (i, j) with a_i XOR b_j equal to the query
+// contributes i^k c_a c_b.  For each query and each left term i the matching
+// right terms are found by looking up (query XOR a_i) in an ordered map of B's
+// keys.  Queries are SoA (nq terms).  Writes coefficient, sum |contribution|
+// and contribution count per query.
+void oracle_query_product_coeffs(int n, int64_t na, const uint64_t* ax, const uint64_t* az,
+                                 const double* ac, const uint8_t* ka, int64_t nb, const uint64_t* bx,
+                                 const uint64_t* bz, const double* bc, const uint8_t* kb, int64_t nq,
+                                 const uint64_t* qx, const uint64_t* qz, double* oc, double* oabs,
+                                 int64_t* ocount) {
+    int W = words_for(n);
+    std::map<std::vector<uint64_t>, std::vector<int64_t>> bmap;
+    for (int64_t j = 0; j < nb; ++j) bmap[key_of(load_term(W, nb, bx, bz, j))].push_back(j);
+    std::vector<Str> as;
+    as.reserve(na);
+    for (int64_t i = 0; i < na; ++i) as.push_back(load_term(W, na, ax, az, i));
+    for (int64_t q = 0; q < nq; ++q) {
+        Str want = load_term(W, nq, qx, qz, q);
+        Acc acc;
+        for (int64_t i = 0; i < na; ++i) {
+            Str need; need.x.assign(W, 0); need.z.assign(W, 0);
+            for (int w = 0; w < W; ++w) { need.x[w] = want.x[w] ^ as[i].x[w]; need.z[w] = want.z[w] ^ as[i].z[w]; }
+            auto it = bmap.find(key_of(need));
+            if (it == bmap.end()) continue;
+            for (int64_t j : it->second) {
+                Str b = load_term(W, nb, bx, bz, j);
+                Str o;
+                int k = string_product(n, as[i], b, &o);
+                k = (k + (ka ? ka[i] : 0) + (kb ? kb[j] : 0)) % 4;
+                Cplx ca = load_coef(ac, i), cb = load_coef(bc, j);
+                Cplx c = rot(cmul(ca, cb), k);
+                acc.re.add(c.re); acc.im.add(c.im);
+                acc.abs_sum += std::hypot(ca.re, ca.im) * std::hypot(cb.re, cb.im);
+                acc.count += 1;
+            }
+        }
+        oc[2 * q] = acc.re.value(); oc[2 * q + 1] = acc.im.value();
+        oabs[q] = acc.abs_sum; ocount[q] = acc.count;
+    }
+}
+
+// Compensated sum of n doubles (exposed so the tests can pin the summation
+// against a correctly rounded library sum).
+double oracle_compensated_sum(int64_t n, const double* v) {
+    Neumaier s;
+    for (int64_t t = 0; t < n; ++t) s.add(v[t]);
+    return s.value();
+}
+
+}  // extern "C"
