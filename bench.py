@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark: merged Pauli products per second for H*H on one GB300.
+
+A step is one canonical product C = H*H (outer product of every term pair,
+then sort by symplectic key and merge duplicates, PauLIB Sec. III-G / IV-C)
+of a seeded, synthetic Jordan-Wigner-shaped Hamiltonian, with the inputs
+already resident in HBM.  Between timed steps a 512 MiB buffer is written to
+flush L2 (the inputs are smaller than L2).  The device time of each step is
+taken with CUDA events on the stream the library launches on.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "merged Pauli products/s (H·H), mixed vs FP64 at equal error; % of roofline"
+UNIT = "products/s"
+HBM_PEAK_FALLBACK = 6800.0
+# FP64 peak derived from unit counts: 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+
+WORKLOADS = {
+    "jw_hh_n200_m30000": dict(n=200, m=30000, seed=401),
+    "jw_hh_n100_m20000": dict(n=100, m=20000, seed=301),
+    "jw_hh_n100_m2000": dict(n=100, m=2000, seed=301),
+}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_PEAK_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(name):
+    from paper_2605_25974_gb300 import workloads as wl
+    cfg = WORKLOADS[name]
+    h = wl.jw(n=cfg["n"], m=cfg["m"], seed=cfg["seed"])
+    return h
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+
+def oracle_rate(h, budget_s=10.0):
+    """The oracle as it stands, single-threaded, on a bounded sample: the
+    canonical product of the first m' terms of H with themselves."""
+    from oracle import pauli_oracle
+    pauli_oracle._load()
+
+    def run(mp):
+        s = h.subset(slice(0, mp))
+        t0 = time.perf_counter()
+        pauli_oracle.multiply_canonical(h.n, s.as_tuple(), s.as_tuple())
+        return time.perf_counter() - t0
+
+    probe = 200
+    t = run(probe)
+    rate = probe * probe / max(t, 1e-6)
+    mp = int(min(h.m, max(probe, (rate * budget_s) ** 0.5)))
+    t = run(mp)
+    return {"value": mp * mp / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "canonical product of the first %d terms of H with themselves (%d products, %.1f s)"
+                      % (mp, mp * mp, t)}, mp
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    h = make_workload(args.workload)
+    from oracle import pauli_oracle
+    base, mp = oracle_rate(h, budget_s=min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    s = h.subset(slice(0, mp))
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        pauli_oracle.multiply_canonical(h.n, s.as_tuple(), s.as_tuple())
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    value = mp * mp / (ms / 1e3)
+    base["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "terms": h.m, "n_qubits": h.n, "sample_terms": mp},
+            "cpu_baseline": base,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2605_25974_gb300 import paulib
+    paulib.load()
+
+    h = make_workload(args.workload)
+    products = h.m * h.m
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    gh = paulib.PauliSum.from_arrays(h)
+
+    def step(prec="fp64"):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = paulib.multiply(gh, gh, prec)
+        e1.record(stream)
+        return out, e0, e1
+
+    for _ in range(args.warmup):
+        out, _, _ = step()
+        U = out.n_terms
+        out.close()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    paulib.timing_read(reset=True)
+    paulib.timing_enable(True)
+    step_ms = []
+    for k in range(args.steps):
+        flush.fill_(k)
+        out, e0, e1 = step()
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        U = out.n_terms
+        out.close()
+    torch.cuda.synchronize()
+    paulib.timing_enable(False)
+    stage_ms, stage_launches = paulib.timing_read(reset=True)
+    barrier()
+    clk = clocks.stop()
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = products * world / (ms / 1e3)
+
+    # ---- mixed precision on the same input (speed and error vs the FP64 result)
+    W = h.x.shape[0]
+    ref = paulib.multiply(gh, gh, "fp64")
+    rx = torch.empty((W, U), dtype=torch.int64, device="cuda")
+    rz = torch.empty_like(rx)
+    rc = torch.empty((U, 2), dtype=torch.float64, device="cuda")
+    ref.export(rx, rz, rc, None, stream=stream)
+    ref.close()
+    dx, dz, dc = torch.empty_like(rx), torch.empty_like(rz), torch.empty_like(rc)
+    rmag = torch.clamp(torch.linalg.vector_norm(rc, dim=1), min=1e-300)
+    precision = {}
+    for prec in ("fp32_fp64merge", "fp32_twosum"):
+        for _ in range(2):
+            o, _, _ = step(prec)
+            o.close()
+        tms = []
+        for k in range(max(2, args.steps // 2)):
+            flush.fill_(k)
+            o, e0, e1 = step(prec)
+            torch.cuda.synchronize()
+            tms.append(e0.elapsed_time(e1))
+            if k == 0:
+                assert o.n_terms == U
+                o.export(dx, dz, dc, None, stream=stream)
+                assert torch.equal(dx, rx) and torch.equal(dz, rz), "mixed-precision key set differs"
+                err = torch.amax(torch.abs(dc - rc), dim=1)
+                rel = (err / rmag).float()
+                srt = torch.sort(rel[:: max(1, U // 4_000_000)]).values
+                stats = {"max_abs_err_vs_fp64": float(err.max()),
+                         "max_rel_err_vs_fp64": float(rel.max()),
+                         "p99_rel_err_vs_fp64": float(srt[int(0.99 * (len(srt) - 1))]),
+                         "median_rel_err_vs_fp64": float(srt[(len(srt) - 1) // 2])}
+            o.close()
+        pm = statistics.mean(tms)
+        precision[prec] = dict(ms_per_step=pm, value=products / (pm / 1e3), speedup_vs_fp64=ms / pm, **stats)
+    del rx, rz, rc, dx, dz, dc, rmag
+
+    # ---- end to end through the C ABI with host buffers
+    hx = torch.from_numpy(h.x.view(np.int64)).pin_memory()
+    hz = torch.from_numpy(h.z.view(np.int64)).pin_memory()
+    hc = torch.from_numpy(h.c.view(np.float64)).pin_memory()
+    ox = torch.empty((W, U), dtype=torch.int64).pin_memory()
+    oz = torch.empty((W, U), dtype=torch.int64).pin_memory()
+    oc = torch.empty((U, 2), dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + max(2, args.steps // 2)):
+        flush.fill_(k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = paulib.PauliSum.create(h.n, hx, hz, hc, stream=stream)
+        o = paulib.multiply(g, g, "fp64")
+        o.export(ox, oz, oc, None, stream=stream)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) * 1e3
+        if k >= args.warmup:
+            e2e_ms.append(dt)
+        o.close()
+        g.close()
+    e2e = statistics.mean(e2e_ms)
+    h2d = hx.numel() * 8 + hz.numel() * 8 + hc.numel() * 8
+    d2h = (ox.numel() + oz.numel() + oc.numel()) * 8
+
+    # ---- roofline of the dominant stage
+    hbm_peak, peak_src = measured_peaks()
+    dom = max(stage_ms, key=lambda s: stage_ms[s])
+    dom_ms = stage_ms[dom] / args.steps
+    WP = 1
+    while WP < W:
+        WP *= 2
+    if dom == "level2":
+        # compulsory traffic of the range kernel: read each record (4 B) and
+        # write each merged term once (2*WP words + complex128) to staging
+        bytes_per = products * 4 + U * (16 * WP + 16)
+        flops = products * 6 + 2 * (products - U)
+        t_hbm = bytes_per / (hbm_peak * 1e9)
+        t_fp = flops / (FP64_PEAK_TFLOPS * 1e12)
+        if t_fp > t_hbm:
+            roof = {"bound": "alu", "achieved": flops / (dom_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "peak_source": "derived FP64 (2 DFMA/clk/SM x 152 SMs x 2.07 GHz)"}
+        else:
+            roof = {"bound": "hbm", "achieved": bytes_per / (dom_ms / 1e3) / 1e9, "peak": hbm_peak,
+                    "unit": "GB/s", "peak_source": peak_src}
+    else:
+        bytes_per = products * 4
+        roof = {"bound": "hbm", "achieved": bytes_per / (dom_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "peak_source": peak_src}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = dom
+    roof["kernel_ms_per_step"] = dom_ms
+    roof["stage_ms_per_step"] = {k: v / args.steps for k, v in stage_ms.items()}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n_qubits": h.n, "terms": h.m, "products": products,
+                       "distinct_out": U, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "512 MiB flush between timed steps"},
+            "roofline": roof, "precision": precision,
+            "e2e": {"value": products / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
+            "gpu_launches": int(sum(stage_launches.values())),
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_rate(h)[0]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    gh.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="jw_hh_n200_m30000", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * paulib.h -- C ABI of the GB300 (sm_103a) Pauli-sum library.
+ *
+ * The library computes the Pauli-sum outer product and its canonical form as
+ * defined in PauLIB (arXiv 2605.25974):
+ *
+ *   - A Pauli sum is H = sum_j c_j P_j with complex c_j and n-qubit Pauli
+ *     strings P_j (Sec. III-A, Eq. 2).
+ *   - A string is stored in the binary symplectic form (x|z) (Sec. III-C,
+ *     Table I: I=(0,0), Z=(0,1), X=(1,0), Y=(1,1)), packed into W = ceil(n/64)
+ *     64-bit X-words and W Z-words.  Qubit q is bit q%64 of word q/64 (the
+ *     paper fixes the word index, Sec. III-F; the bit order is this library's).
+ *     Bits at qubit >= n of the last word must be zero.
+ *   - The product of two strings XORs their words; its phase i^k follows from
+ *     popcounts of the words (Sec. III-E).  Concretely, with
+ *     P(x,z) = i^{|x&z|} X^x Z^z, the product P_a P_b equals i^k P(x_a^x_b,
+ *     z_a^z_b) with k = |x_a&z_a| + |x_b&z_b| + 2|z_a&x_b| - |x&z| (mod 4).
+ *   - The product of two sums is the outer product: every left term times
+ *     every right term, |A|*|B| products (Sec. IV-B, IV-C, V-C).
+ *   - The canonical form sorts terms by a lexicographic key of the packed
+ *     words and merges equal strings by adding their coefficients
+ *     (Sec. III-G).  Key = (x_0..x_{W-1}, z_0..z_{W-1}) compared as unsigned
+ *     64-bit words, word 0 most significant.  Strings whose merged coefficient
+ *     is exactly zero are kept.
+ *
+ * Conventions for every call:
+ *   - Sums are opaque, device resident and owned by the library.  A sum is
+ *     immutable after creation; destroy it with paulib_sum_destroy.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     stream ordered; a call returns once its work is enqueued, except where
+ *     noted (calls that must learn an output size synchronise `stream` once).
+ *   - Array arguments may be host or device pointers (CUDA unified addressing
+ *     decides); host arrays are copied through the stream.
+ *   - No call aborts or throws.  A non-OK status leaves outputs untouched
+ *     (output handles are set to NULL) and records a message readable with
+ *     paulib_last_error() on the calling thread.
+ *   - Only one GPU is used: the device current on the calling thread.
+ */
+#ifndef PAULIB_H
+#define PAULIB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PAULIB_ABI_VERSION 1
+#define PAULIB_MAX_QUBITS 1024
+
+typedef struct paulib_sum paulib_sum;
+
+typedef enum paulib_status {
+    PAULIB_OK = 0,
+    PAULIB_ERR_INVALID_ARG = 1,     /* bad pointer, size or enum value            */
+    PAULIB_ERR_QUBIT_MISMATCH = 2,  /* operands have different qubit counts       */
+    PAULIB_ERR_TAIL_BITS = 3,       /* a bit at qubit >= n is set                  */
+    PAULIB_ERR_OOM = 4,             /* device allocation failed                    */
+    PAULIB_ERR_CUDA = 5,            /* a CUDA runtime call failed                  */
+    PAULIB_ERR_TIMEOUT = 6,         /* a bounded device wait expired               */
+    PAULIB_ERR_UNSUPPORTED = 7,     /* size beyond this build's limits             */
+    PAULIB_ERR_INTERNAL = 8         /* an internal consistency check failed        */
+} paulib_status;
+
+/* Arithmetic of the coefficient products and of the duplicate merge.  The
+ * phase exponent and the key set are exact integers in every mode; outputs
+ * are always complex128.  (The paper keeps a real double plus 2 phase bits,
+ * Sec. III-C; this library keeps complex coefficients as in Eq. 2.)         */
+typedef enum paulib_precision {
+    PAULIB_FP64 = 0,                    /* FP64 products, FP64 merge             */
+    PAULIB_FP32_MUL_FP64_MERGE = 1,     /* FP32 products widened to FP64 sums    */
+    PAULIB_FP32_MUL_TWOSUM_MERGE = 2    /* FP32 products, FP32 TwoSum-compensated merge */
+} paulib_precision;
+
+enum { PAULIB_OUT_RAW = 0, PAULIB_OUT_CANONICAL = 1 };
+
+int32_t paulib_abi_version(void);
+
+/* Creates a sum of n_terms n-qubit terms (1 <= n_qubits <= 1024, n_terms >= 0).
+ *   x_words, z_words: struct-of-arrays as in the paper's PauliSumSoA
+ *       (Sec. IV-A): word w of term t at [w * n_terms + t], W = ceil(n/64)
+ *       words per term.  NULL allowed only when n_terms == 0.
+ *   coeffs: complex128 interleaved (re, im), n_terms entries.
+ *   phase:  optional (NULL = all zero) exponents k in 0..3; term t is then
+ *       i^k[t] * c[t] * P[t].  Higher bits are ignored.
+ * Any order and repeated strings are accepted.  The library copies the data;
+ * the caller keeps ownership of its arrays.  Synchronises `stream` once to
+ * validate the tail bits (PAULIB_ERR_TAIL_BITS).                            */
+paulib_status paulib_sum_create(int32_t n_qubits, int64_t n_terms, const uint64_t* x_words,
+                                const uint64_t* z_words, const double* coeffs, const uint8_t* phase,
+                                void* stream, paulib_sum** out);
+
+/* Size and shape of a sum.  Any output pointer may be NULL. */
+paulib_status paulib_sum_info(const paulib_sum* s, int32_t* n_qubits, int64_t* n_terms,
+                              int32_t* is_canonical);
+
+/* Copies a sum out in the paulib_sum_create layout (host or device arrays of
+ * at least W*n_terms words / n_terms coefficients).  `phase` may be NULL; a
+ * canonical sum has all phases zero.  Stream ordered: host arrays are valid
+ * after `stream` is synchronised.                                           */
+paulib_status paulib_sum_export(const paulib_sum* s, uint64_t* x_words, uint64_t* z_words,
+                                double* coeffs, uint8_t* phase, void* stream);
+
+void paulib_sum_destroy(paulib_sum* s);
+
+/* Outer product A*B (Sec. IV-C, V-C): every pair a_i * b_j, A on the left.
+ *   out_kind PAULIB_OUT_RAW: |A|*|B| terms, product (i, j) at index
+ *       j*|A| + i (one block of |A| per right term, Sec. IV-C); term phase =
+ *       k_a + k_b + k_pair (mod 4); coefficient c_a*c_b (not rotated).
+ *       `precision` must be PAULIB_FP64.
+ *   out_kind PAULIB_OUT_CANONICAL: the canonical form (Sec. III-G) of the
+ *       product: distinct strings in ascending key order, coefficient =
+ *       sum over contributing pairs of i^k c_a c_b.  Synchronises `stream`
+ *       once to learn the number of distinct strings.
+ * Requires |A|*|B| < 2^32 for the canonical form (PAULIB_ERR_UNSUPPORTED
+ * otherwise).  An empty operand gives an empty result.                      */
+paulib_status paulib_multiply(const paulib_sum* a, const paulib_sum* b, int32_t precision,
+                              int32_t out_kind, void* stream, paulib_sum** out);
+
+/* Canonical form of one sum (Sec. III-G, sort_and_combine): a term with
+ * phase k contributes i^k * c.  Synchronises `stream` once.                 */
+paulib_status paulib_compress(const paulib_sum* in, int32_t precision, void* stream,
+                              paulib_sum** out);
+
+/* `batch` independent canonical products out[b] = canonical(a[b] * b[b]).
+ * All operands must share one qubit count.  Products are processed together
+ * as one canonicalisation of keys prefixed by the problem index.            */
+paulib_status paulib_multiply_batched(int32_t batch, const paulib_sum* const* a,
+                                      const paulib_sum* const* b, int32_t precision, void* stream,
+                                      paulib_sum** out);
+
+/* Message for the last non-OK status returned on this thread ("" if none). */
+const char* paulib_last_error(void);
+
+/* Replaces the device allocator (NULL, NULL restores the default stream-
+ * ordered cudaMallocAsync/cudaFreeAsync).  alloc returns NULL on failure
+ * (reported as PAULIB_ERR_OOM).  Memory is freed through free_ on the stream
+ * that last used it.  Not thread safe against concurrent calls.            */
+typedef void* (*paulib_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*paulib_free_fn)(void* ptr, void* stream, void* ctx);
+paulib_status paulib_set_allocator(paulib_alloc_fn alloc, paulib_free_fn free_, void* ctx);
+
+/* Diagnostics (no counterpart in the paper): device time of the library's
+ * stages measured with CUDA events recorded on the launching stream, and the
+ * number of kernels launched per stage.  Stages:
+ *   0 input conversion, 1 splitter sampling and selection, 2 coarse count,
+ *   3 coarse scatter, 4 range sort + merge (the per-range worklist kernel),
+ *   5 output compaction, 6 raw outer product, 7 export.
+ * paulib_timing_enable(1) starts recording (0 stops).  paulib_timing_read
+ * waits for recorded events, adds their times to ms[PAULIB_STAGES] and the
+ * launch counts to launches[PAULIB_STAGES] (either may be NULL), and clears
+ * the totals when `reset` is nonzero.  Launch counts are kept even when
+ * event timing is off.                                                      */
+#define PAULIB_STAGES 8
+paulib_status paulib_timing_enable(int32_t on);
+paulib_status paulib_timing_read(double* ms, int64_t* launches, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAULIB_H */

@@ -1,0 +1,441 @@
+// paulib_api.cu -- the C ABI (include/paulib.h): argument checks, memory
+// management, host<->device staging, and dispatch to the kernels.
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <new>
+#include <vector>
+#include "paulib_internal.h"
+
+namespace paulib {
+
+namespace {
+thread_local std::string g_last_error;
+paulib_alloc_fn g_alloc = nullptr;
+paulib_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+std::mutex g_pool_mu;
+bool g_pool_configured[64] = {};
+}  // namespace
+
+void fail(paulib_status st, const std::string& msg) { throw Error{st, msg}; }
+
+void check_cuda(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (e == cudaErrorMemoryAllocation) fail(PAULIB_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+        fail(PAULIB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+}
+
+static void configure_pool_once() {
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev < 0 || dev >= 64 || g_pool_configured[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        // Keep freed blocks cached in the pool instead of returning them to
+        // the driver at every synchronisation.
+        uint64_t thr = std::numeric_limits<uint64_t>::max();
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    g_pool_configured[dev] = true;
+}
+
+void* dev_alloc(size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return nullptr;
+    if (g_alloc) {
+        void* p = g_alloc(bytes, (void*)s, g_alloc_ctx);
+        if (!p) fail(PAULIB_ERR_OOM, "allocator callback returned NULL for " + std::to_string(bytes) + " bytes");
+        return p;
+    }
+    configure_pool_once();
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        fail(PAULIB_ERR_OOM, "cudaMallocAsync(" + std::to_string(bytes) + ") failed: " + cudaGetErrorString(e));
+    }
+    return p;
+}
+
+void dev_free(void* p, cudaStream_t s) {
+    if (!p) return;
+    if (g_free) { g_free(p, (void*)s, g_alloc_ctx); return; }
+    cudaFreeAsync(p, s);
+}
+
+int padded_words(int W) {
+    int wp = 1;
+    while (wp < W) wp *= 2;
+    return wp;
+}
+
+int device_sm_count() {
+    static int cached[64] = {};
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+    int n = 0;
+    check_cuda(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev), "sm count");
+    if (dev >= 0 && dev < 64) cached[dev] = n;
+    return n;
+}
+
+// ---------------------------------------------------------------- stage timing
+
+namespace {
+struct TimedSpan {
+    int stage;
+    cudaEvent_t a, b;
+};
+std::mutex g_t_mu;
+bool g_timing = false;
+int g_depth = 0;
+int g_outer_stage = -1;
+std::vector<TimedSpan> g_spans;
+std::vector<cudaEvent_t> g_event_pool;
+double g_ms[PAULIB_STAGES] = {};
+int64_t g_launches[PAULIB_STAGES] = {};
+
+cudaEvent_t take_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+}  // namespace
+
+StageScope::StageScope(int st, cudaStream_t str) : stage(st), s(str), outer(false) {
+    std::lock_guard<std::mutex> lk(g_t_mu);
+    if (g_depth++ == 0) {
+        outer = true;
+        g_outer_stage = st;
+        if (g_timing) {
+            a = take_event();
+            if (a && cudaEventRecord(a, s) != cudaSuccess) {
+                cudaGetLastError();
+                g_event_pool.push_back(a);
+                a = nullptr;
+            }
+        }
+    }
+}
+
+StageScope::~StageScope() {
+    std::lock_guard<std::mutex> lk(g_t_mu);
+    --g_depth;
+    if (outer) {
+        g_outer_stage = -1;
+        if (a) {
+            cudaEvent_t b = take_event();
+            if (b && cudaEventRecord(b, s) == cudaSuccess) g_spans.push_back(TimedSpan{stage, a, b});
+            else g_event_pool.push_back(a);
+        }
+    }
+}
+
+void note_launch(int stage) {
+    std::lock_guard<std::mutex> lk(g_t_mu);
+    const int st = g_outer_stage >= 0 ? g_outer_stage : stage;
+    if (st >= 0 && st < PAULIB_STAGES) g_launches[st] += 1;
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+paulib_sum* sum_alloc(int32_t n_qubits, int64_t n_terms, bool with_phase, cudaStream_t s) {
+    paulib_sum* r = new (std::nothrow) paulib_sum;
+    if (!r) fail(PAULIB_ERR_OOM, "host allocation failed");
+    r->n_qubits = n_qubits;
+    r->W = (n_qubits + 63) / 64;
+    r->WP = padded_words(r->W);
+    r->n_terms = n_terms;
+    check_cuda(cudaGetDevice(&r->device), "cudaGetDevice");
+    r->stream = s;
+    const size_t nt = (size_t)n_terms;
+    const size_t kb = align_up(nt * 2 * r->WP * sizeof(uint64_t), 256);
+    const size_t cb = align_up(nt * sizeof(double2), 256);
+    const size_t pb = align_up(nt, 256);
+    const size_t hb = with_phase ? align_up(nt, 256) : 0;
+    r->block_bytes = kb + cb + pb + hb;
+    if (n_terms > 0) {
+        try {
+            r->block = dev_alloc(r->block_bytes, s);
+        } catch (...) {
+            delete r;
+            throw;
+        }
+        char* base = static_cast<char*>(r->block);
+        r->keys = reinterpret_cast<uint64_t*>(base);
+        r->coef = reinterpret_cast<double2*>(base + kb);
+        r->pbase = reinterpret_cast<uint8_t*>(base + kb + cb);
+        r->phase = with_phase ? reinterpret_cast<uint8_t*>(base + kb + cb + pb) : nullptr;
+    }
+    return r;
+}
+
+void sum_free(paulib_sum* s, cudaStream_t st) {
+    if (!s) return;
+    if (s->block) dev_free(s->block, st);
+    delete s;
+}
+
+static bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Returns a device pointer holding `bytes` of `src` (staging host data).
+static const void* to_device(const void* src, size_t bytes, cudaStream_t s, Scratch& keep) {
+    if (!src || bytes == 0) return src;
+    if (is_device_ptr(src)) return src;
+    keep = Scratch(bytes, s);
+    check_cuda(cudaMemcpyAsync(keep.p, src, bytes, cudaMemcpyHostToDevice, s), "host-to-device copy");
+    return keep.p;
+}
+
+}  // namespace paulib
+
+using namespace paulib;
+
+#define PAULIB_API_BEGIN try {
+#define PAULIB_API_END                                             \
+    }                                                              \
+    catch (const Error& e) {                                       \
+        g_last_error = e.msg;                                      \
+        return e.status;                                           \
+    }                                                              \
+    catch (const std::bad_alloc&) {                                \
+        g_last_error = "host allocation failed";                   \
+        return PAULIB_ERR_OOM;                                     \
+    }                                                              \
+    catch (...) {                                                  \
+        g_last_error = "unexpected internal exception";            \
+        return PAULIB_ERR_INTERNAL;                                \
+    }
+
+extern "C" {
+
+int32_t paulib_abi_version(void) { return PAULIB_ABI_VERSION; }
+
+const char* paulib_last_error(void) { return g_last_error.c_str(); }
+
+paulib_status paulib_set_allocator(paulib_alloc_fn alloc, paulib_free_fn free_, void* ctx) {
+    if ((alloc == nullptr) != (free_ == nullptr)) {
+        g_last_error = "allocator and free callbacks must both be set or both be NULL";
+        return PAULIB_ERR_INVALID_ARG;
+    }
+    g_alloc = alloc;
+    g_free = free_;
+    g_alloc_ctx = ctx;
+    return PAULIB_OK;
+}
+
+paulib_status paulib_sum_create(int32_t n_qubits, int64_t n_terms, const uint64_t* x_words,
+                                const uint64_t* z_words, const double* coeffs, const uint8_t* phase,
+                                void* stream, paulib_sum** out) {
+    if (out) *out = nullptr;
+    PAULIB_API_BEGIN
+    if (!out) fail(PAULIB_ERR_INVALID_ARG, "out is NULL");
+    if (n_qubits < 1 || n_qubits > PAULIB_MAX_QUBITS)
+        fail(PAULIB_ERR_INVALID_ARG, "n_qubits must be in 1..1024, got " + std::to_string(n_qubits));
+    if (n_terms < 0) fail(PAULIB_ERR_INVALID_ARG, "n_terms must be >= 0");
+    if (n_terms > 0 && (!x_words || !z_words || !coeffs))
+        fail(PAULIB_ERR_INVALID_ARG, "x_words, z_words and coeffs must be non-NULL when n_terms > 0");
+    if (n_terms > ((int64_t)1 << 40)) fail(PAULIB_ERR_UNSUPPORTED, "n_terms too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    paulib_sum* r = sum_alloc(n_qubits, n_terms, phase != nullptr, s);
+    try {
+        if (n_terms > 0) {
+            const size_t wbytes = (size_t)r->W * (size_t)n_terms * sizeof(uint64_t);
+            Scratch kx, kz, kc, kp;
+            const uint64_t* dx = (const uint64_t*)to_device(x_words, wbytes, s, kx);
+            const uint64_t* dz = (const uint64_t*)to_device(z_words, wbytes, s, kz);
+            const double* dc = (const double*)to_device(coeffs, (size_t)n_terms * 16, s, kc);
+            const uint8_t* dp = (const uint8_t*)to_device(phase, (size_t)n_terms, s, kp);
+            Scratch flag(sizeof(int32_t), s);
+            check_cuda(cudaMemsetAsync(flag.p, 0, sizeof(int32_t), s), "memset");
+            launch_create(r, dx, dz, dc, dp, flag.as<int32_t>(), s);
+            int32_t h = 0;
+            check_cuda(cudaMemcpyAsync(&h, flag.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "flag copy");
+            check_cuda(cudaStreamSynchronize(s), "create sync");
+            if (h) fail(PAULIB_ERR_TAIL_BITS, "a bit at qubit >= n_qubits is set in the last word");
+        }
+    } catch (...) {
+        sum_free(r, s);
+        throw;
+    }
+    *out = r;
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_sum_info(const paulib_sum* s, int32_t* n_qubits, int64_t* n_terms,
+                              int32_t* is_canonical) {
+    PAULIB_API_BEGIN
+    if (!s) fail(PAULIB_ERR_INVALID_ARG, "sum is NULL");
+    if (n_qubits) *n_qubits = s->n_qubits;
+    if (n_terms) *n_terms = s->n_terms;
+    if (is_canonical) *is_canonical = s->is_canonical;
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_sum_export(const paulib_sum* s, uint64_t* x_words, uint64_t* z_words,
+                                double* coeffs, uint8_t* phase, void* stream) {
+    PAULIB_API_BEGIN
+    if (!s) fail(PAULIB_ERR_INVALID_ARG, "sum is NULL");
+    if (s->n_terms == 0) return PAULIB_OK;
+    if (!x_words || !z_words || !coeffs) fail(PAULIB_ERR_INVALID_ARG, "output arrays must be non-NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nt = (size_t)s->n_terms;
+    const size_t wbytes = (size_t)s->W * nt * sizeof(uint64_t);
+    const bool dx = is_device_ptr(x_words), dz = is_device_ptr(z_words), dc = is_device_ptr(coeffs);
+    const bool dp = phase ? is_device_ptr(phase) : true;
+    Scratch sx, sz, sc, sp;
+    uint64_t* tx = x_words;
+    uint64_t* tz = z_words;
+    double* tc = coeffs;
+    uint8_t* tp = phase;
+    if (!dx) { sx = Scratch(wbytes, st); tx = sx.as<uint64_t>(); }
+    if (!dz) { sz = Scratch(wbytes, st); tz = sz.as<uint64_t>(); }
+    if (!dc) { sc = Scratch(nt * 16, st); tc = sc.as<double>(); }
+    if (phase && !dp) { sp = Scratch(nt, st); tp = sp.as<uint8_t>(); }
+    launch_export(s, tx, tz, tc, tp, st);
+    if (!dx) check_cuda(cudaMemcpyAsync(x_words, tx, wbytes, cudaMemcpyDeviceToHost, st), "export copy");
+    if (!dz) check_cuda(cudaMemcpyAsync(z_words, tz, wbytes, cudaMemcpyDeviceToHost, st), "export copy");
+    if (!dc) check_cuda(cudaMemcpyAsync(coeffs, tc, nt * 16, cudaMemcpyDeviceToHost, st), "export copy");
+    if (phase && !dp) check_cuda(cudaMemcpyAsync(phase, tp, nt, cudaMemcpyDeviceToHost, st), "export copy");
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+void paulib_sum_destroy(paulib_sum* s) {
+    if (!s) return;
+    try {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != s->device) cudaSetDevice(s->device);
+        sum_free(s, s->stream);
+        if (cur != s->device) cudaSetDevice(cur);
+    } catch (...) {
+    }
+}
+
+static void check_pair(const paulib_sum* a, const paulib_sum* b) {
+    if (!a || !b) fail(PAULIB_ERR_INVALID_ARG, "operand is NULL");
+    if (a->n_qubits != b->n_qubits)
+        fail(PAULIB_ERR_QUBIT_MISMATCH, "operands have " + std::to_string(a->n_qubits) + " and " +
+                                            std::to_string(b->n_qubits) + " qubits");
+}
+
+static void check_mode(int32_t precision) {
+    if (precision < PAULIB_FP64 || precision > PAULIB_FP32_MUL_TWOSUM_MERGE)
+        fail(PAULIB_ERR_INVALID_ARG, "unknown precision mode " + std::to_string(precision));
+}
+
+paulib_status paulib_multiply(const paulib_sum* a, const paulib_sum* b, int32_t precision,
+                              int32_t out_kind, void* stream, paulib_sum** out) {
+    if (out) *out = nullptr;
+    PAULIB_API_BEGIN
+    if (!out) fail(PAULIB_ERR_INVALID_ARG, "out is NULL");
+    check_pair(a, b);
+    check_mode(precision);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (out_kind == PAULIB_OUT_RAW) {
+        if (precision != PAULIB_FP64) fail(PAULIB_ERR_INVALID_ARG, "raw products are FP64 only");
+        const int64_t n = a->n_terms * b->n_terms;
+        if (a->n_terms > 0 && n / a->n_terms != b->n_terms) fail(PAULIB_ERR_UNSUPPORTED, "size overflow");
+        paulib_sum* r = sum_alloc(a->n_qubits, n, true, s);
+        try {
+            if (n > 0) launch_outer_raw(a, b, r, s);
+        } catch (...) {
+            sum_free(r, s);
+            throw;
+        }
+        *out = r;
+        return PAULIB_OK;
+    }
+    if (out_kind != PAULIB_OUT_CANONICAL) fail(PAULIB_ERR_INVALID_ARG, "unknown out_kind");
+    *out = canon_product(a, b, precision, s);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_compress(const paulib_sum* in, int32_t precision, void* stream,
+                              paulib_sum** out) {
+    if (out) *out = nullptr;
+    PAULIB_API_BEGIN
+    if (!out || !in) fail(PAULIB_ERR_INVALID_ARG, "NULL argument");
+    check_mode(precision);
+    *out = canon_terms(in, precision, (cudaStream_t)stream);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_multiply_batched(int32_t batch, const paulib_sum* const* a,
+                                      const paulib_sum* const* b, int32_t precision, void* stream,
+                                      paulib_sum** out) {
+    PAULIB_API_BEGIN
+    if (batch < 0) fail(PAULIB_ERR_INVALID_ARG, "batch < 0");
+    if (batch == 0) return PAULIB_OK;
+    if (!a || !b || !out) fail(PAULIB_ERR_INVALID_ARG, "NULL array argument");
+    for (int32_t i = 0; i < batch; ++i) out[i] = nullptr;
+    check_mode(precision);
+    for (int32_t i = 0; i < batch; ++i) {
+        check_pair(a[i], b[i]);
+        if (a[i]->n_qubits != a[0]->n_qubits)
+            fail(PAULIB_ERR_QUBIT_MISMATCH, "batched operands must share one qubit count");
+    }
+    canon_batched(batch, a, b, precision, (cudaStream_t)stream, out);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_timing_enable(int32_t on) {
+    std::lock_guard<std::mutex> lk(g_t_mu);
+    g_timing = on != 0;
+    return PAULIB_OK;
+}
+
+paulib_status paulib_timing_read(double* ms, int64_t* launches, int32_t reset) {
+    PAULIB_API_BEGIN
+    std::lock_guard<std::mutex> lk(g_t_mu);
+    for (const TimedSpan& sp : g_spans) {
+        float t = 0.f;
+        check_cuda(cudaEventSynchronize(sp.b), "cudaEventSynchronize");
+        check_cuda(cudaEventElapsedTime(&t, sp.a, sp.b), "cudaEventElapsedTime");
+        if (sp.stage >= 0 && sp.stage < PAULIB_STAGES) g_ms[sp.stage] += t;
+        g_event_pool.push_back(sp.a);
+        g_event_pool.push_back(sp.b);
+    }
+    g_spans.clear();
+    for (int i = 0; i < PAULIB_STAGES; ++i) {
+        if (ms) ms[i] = g_ms[i];
+        if (launches) launches[i] = g_launches[i];
+        if (reset) {
+            g_ms[i] = 0.0;
+            g_launches[i] = 0;
+        }
+    }
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+}  // extern "C"

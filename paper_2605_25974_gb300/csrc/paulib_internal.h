@@ -1,0 +1,108 @@
+// paulib_internal.h -- host-side internals shared by the library's .cu files.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <cuda_runtime.h>
+#include "../../include/paulib.h"
+
+// A device-resident Pauli sum.  One allocation holds every array.
+struct paulib_sum {
+    int32_t n_qubits = 0;
+    int32_t W = 0;        // ceil(n/64): words per half at the API boundary
+    int32_t WP = 0;       // padded words per half in device memory (1,2,4,8,16)
+    int64_t n_terms = 0;
+    int32_t is_canonical = 0;
+    int32_t device = 0;
+    cudaStream_t stream = nullptr;  // stream of the call that produced it; destroy frees on it
+    uint64_t* keys = nullptr;   // [n_terms][2*WP] : x words then z words, zero padded
+    double2* coef = nullptr;    // [n_terms] complex128
+    uint8_t* pbase = nullptr;   // [n_terms] (|x&z| + phase) mod 4: exponent in the X^x Z^z form
+    uint8_t* phase = nullptr;   // [n_terms] own phase exponent, or null when all zero
+    void* block = nullptr;      // the single allocation
+    size_t block_bytes = 0;
+};
+
+namespace paulib {
+
+struct Error {
+    paulib_status status;
+    std::string msg;
+};
+
+[[noreturn]] void fail(paulib_status st, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+
+void* dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
+// A scratch buffer freed (stream ordered) when it goes out of scope.
+struct Scratch {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    Scratch() = default;
+    Scratch(size_t bytes, cudaStream_t st) : p(bytes ? dev_alloc(bytes, st) : nullptr), s(st) {}
+    Scratch(const Scratch&) = delete;
+    Scratch& operator=(const Scratch&) = delete;
+    Scratch(Scratch&& o) noexcept : p(o.p), s(o.s) { o.p = nullptr; }
+    Scratch& operator=(Scratch&& o) noexcept {
+        if (this != &o) { release(); p = o.p; s = o.s; o.p = nullptr; }
+        return *this;
+    }
+    ~Scratch() { release(); }
+    void release() { if (p) dev_free(p, s); p = nullptr; }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+int padded_words(int W);
+
+#define PAULIB_DISPATCH_WP(wp, F)                                                   \
+    switch (wp) {                                                                   \
+        case 1: F(1); break;                                                        \
+        case 2: F(2); break;                                                        \
+        case 4: F(4); break;                                                        \
+        case 8: F(8); break;                                                        \
+        case 16: F(16); break;                                                      \
+        default: ::paulib::fail(PAULIB_ERR_INTERNAL, "unsupported padded word count"); \
+    }
+int device_sm_count();
+
+// ---- stage timing (paulib_timing_*): events are recorded only by the
+// outermost active scope, so nested pipelines count toward the outer stage.
+enum Stage : int {
+    ST_CONVERT = 0, ST_SAMPLE = 1, ST_COUNT = 2, ST_SCATTER = 3, ST_LEVEL2 = 4, ST_COMPACT = 5,
+    ST_RAW = 6, ST_EXPORT = 7
+};
+struct StageScope {
+    StageScope(int stage, cudaStream_t s);
+    ~StageScope();
+    StageScope(const StageScope&) = delete;
+    StageScope& operator=(const StageScope&) = delete;
+    int stage;
+    cudaStream_t s;
+    bool outer;
+    cudaEvent_t a = nullptr;
+};
+// Counts one kernel launch toward the outermost active stage (or `stage`
+// when none is active).
+void note_launch(int stage);
+
+// Allocates an empty sum shell with storage for n terms.
+paulib_sum* sum_alloc(int32_t n_qubits, int64_t n_terms, bool with_phase, cudaStream_t s);
+void sum_free(paulib_sum* s, cudaStream_t st);
+
+// ---- conversion kernels (paulib_convert.cu)
+// SoA device arrays -> sum storage; sets *err_flag (device) nonzero when a
+// tail bit is set.
+void launch_create(paulib_sum* s, const uint64_t* x_soa, const uint64_t* z_soa, const double* coef,
+                   const uint8_t* phase, int32_t* err_flag, cudaStream_t st);
+void launch_export(const paulib_sum* s, uint64_t* x_soa, uint64_t* z_soa, double* coef,
+                   uint8_t* phase, cudaStream_t st);
+void launch_outer_raw(const paulib_sum* a, const paulib_sum* b, paulib_sum* out, cudaStream_t st);
+
+// ---- canonicalisation (paulib_canon.cu)
+paulib_sum* canon_product(const paulib_sum* a, const paulib_sum* b, int mode, cudaStream_t st);
+paulib_sum* canon_terms(const paulib_sum* in, int mode, cudaStream_t st);
+void canon_batched(int32_t batch, const paulib_sum* const* a, const paulib_sum* const* b, int mode,
+                   cudaStream_t st, paulib_sum** out);
+
+}  // namespace paulib

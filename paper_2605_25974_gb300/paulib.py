@@ -1,0 +1,221 @@
+"""Thin ctypes binding over ``libpaulib.so`` (declared in ``include/paulib.h``).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  Host arrays are numpy arrays; device arrays are torch
+CUDA tensors (PyTorch provides device memory and streams, nothing else).
+There is no CPU fallback: if the library is missing, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+
+OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "QUBIT_MISMATCH", 3: "TAIL_BITS", 4: "OOM", 5: "CUDA",
+          6: "TIMEOUT", 7: "UNSUPPORTED", 8: "INTERNAL"}
+PRECISION = {"fp64": 0, "fp32_fp64merge": 1, "fp32_twosum": 2}
+OUT_RAW, OUT_CANONICAL = 0, 1
+
+# Every symbol include/paulib.h declares.
+EXPORTED = ["paulib_abi_version", "paulib_sum_create", "paulib_sum_info", "paulib_sum_export",
+            "paulib_sum_destroy", "paulib_multiply", "paulib_compress", "paulib_multiply_batched",
+            "paulib_last_error", "paulib_set_allocator", "paulib_timing_enable", "paulib_timing_read"]
+STAGES = ["convert", "sample", "count", "scatter", "level2", "compact", "raw", "export"]
+
+
+class PaulibError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, str(status)), msg))
+        self.status = status
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load(path: Optional[str] = None):
+    """Opens the library (no build, no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libpaulib.so not found at %s: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)" % p)
+    lib = ctypes.CDLL(p)
+    lib.paulib_abi_version.restype = _i32
+    lib.paulib_sum_create.argtypes = [_i32, _i64, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]
+    lib.paulib_sum_info.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i32)]
+    lib.paulib_sum_export.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+    lib.paulib_sum_destroy.argtypes = [_vp]
+    lib.paulib_sum_destroy.restype = None
+    lib.paulib_multiply.argtypes = [_vp, _vp, _i32, _i32, _vp, ctypes.POINTER(_vp)]
+    lib.paulib_compress.argtypes = [_vp, _i32, _vp, ctypes.POINTER(_vp)]
+    lib.paulib_multiply_batched.argtypes = [_i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32, _vp,
+                                            ctypes.POINTER(_vp)]
+    lib.paulib_last_error.restype = ctypes.c_char_p
+    lib.paulib_timing_enable.argtypes = [_i32]
+    lib.paulib_timing_enable.restype = _i32
+    lib.paulib_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
+    lib.paulib_timing_read.restype = _i32
+    for name in ("paulib_sum_create", "paulib_sum_info", "paulib_sum_export", "paulib_multiply",
+                 "paulib_compress", "paulib_multiply_batched", "paulib_set_allocator"):
+        getattr(lib, name).restype = _i32
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != OK:
+        raise PaulibError(st, load().paulib_last_error().decode(errors="replace"))
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()  # torch tensor
+
+
+def _words(n):
+    return (n + 63) // 64
+
+
+def _prec(p) -> int:
+    return PRECISION[p] if isinstance(p, str) else int(p)
+
+
+class PauliSum:
+    """Owning handle of a device-resident sum."""
+
+    def __init__(self, handle: int):
+        self._h = handle
+        n, m, c = _i32(), _i64(), _i32()
+        _check(load().paulib_sum_info(_vp(handle), ctypes.byref(n), ctypes.byref(m), ctypes.byref(c)))
+        self.n_qubits, self.n_terms, self.is_canonical = n.value, m.value, bool(c.value)
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    @property
+    def words(self) -> int:
+        return _words(self.n_qubits)
+
+    @classmethod
+    def create(cls, n_qubits: int, x, z, c, k=None, stream=None) -> "PauliSum":
+        """x, z: (W, M) uint64; c: (M,) complex128 (or (M, 2) float64); k: (M,) uint8.
+        Host (numpy, contiguous) or device (torch CUDA) arrays."""
+        m = int(x.shape[-1]) if x.ndim == 2 else int(x.shape[0])
+        keep = []
+        arrs = []
+        for a in (x, z, c, k):
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a)
+            keep.append(a)
+            arrs.append(_ptr(a))
+        out = _vp()
+        _check(load().paulib_sum_create(int(n_qubits), int(m), arrs[0], arrs[1], arrs[2], arrs[3],
+                                        _vp(_stream(stream)), ctypes.byref(out)))
+        return cls(out.value)
+
+    @classmethod
+    def from_arrays(cls, s, stream=None) -> "PauliSum":
+        """From a ``workloads.SumArrays``."""
+        return cls.create(s.n, s.x, s.z, s.c, s.k, stream=stream)
+
+    def export(self, x=None, z=None, c=None, k=None, stream=None, with_phase=True):
+        """Copies the sum out (into the given host/device buffers, or new host
+        arrays).  Synchronises the stream before returning host arrays."""
+        W, m = self.words, self.n_terms
+        if x is None:
+            x = np.zeros((W, m), np.uint64)
+            z = np.zeros((W, m), np.uint64)
+            c = np.zeros(m, np.complex128)
+            k = np.zeros(m, np.uint8) if with_phase else None
+        st = _stream(stream)
+        _check(load().paulib_sum_export(_vp(self._h), _ptr(x), _ptr(z), _ptr(c), _ptr(k), _vp(st)))
+        if isinstance(x, np.ndarray) or (hasattr(x, "is_cuda") and not x.is_cuda):
+            import torch
+            if stream is None:
+                torch.cuda.current_stream().synchronize()
+            elif hasattr(stream, "synchronize"):
+                stream.synchronize()
+            else:
+                torch.cuda.synchronize()
+        return x, z, c, k
+
+    def close(self):
+        if self._h:
+            load().paulib_sum_destroy(_vp(self._h))
+            self._h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def multiply(a: PauliSum, b: PauliSum, precision="fp64", canonical: bool = True, stream=None) -> PauliSum:
+    out = _vp()
+    _check(load().paulib_multiply(_vp(a.handle), _vp(b.handle), _prec(precision),
+                                  OUT_CANONICAL if canonical else OUT_RAW, _vp(_stream(stream)),
+                                  ctypes.byref(out)))
+    return PauliSum(out.value)
+
+
+def compress(s: PauliSum, precision="fp64", stream=None) -> PauliSum:
+    out = _vp()
+    _check(load().paulib_compress(_vp(s.handle), _prec(precision), _vp(_stream(stream)), ctypes.byref(out)))
+    return PauliSum(out.value)
+
+
+def multiply_batched(a: Sequence[PauliSum], b: Sequence[PauliSum], precision="fp64",
+                     stream=None) -> List[PauliSum]:
+    n = len(a)
+    A = (_vp * n)(*[s.handle for s in a])
+    B = (_vp * n)(*[s.handle for s in b])
+    O = (_vp * n)()
+    _check(load().paulib_multiply_batched(n, A, B, _prec(precision), _vp(_stream(stream)), O))
+    return [PauliSum(O[i]) for i in range(n)]
+
+
+def timing_enable(on: bool = True):
+    _check(load().paulib_timing_enable(1 if on else 0))
+
+
+def timing_read(reset: bool = True):
+    """Per-stage device milliseconds and kernel launch counts since the last reset."""
+    n = len(STAGES)
+    ms = (ctypes.c_double * n)()
+    la = (_i64 * n)()
+    _check(load().paulib_timing_read(ms, la, 1 if reset else 0))
+    return ({s: ms[i] for i, s in enumerate(STAGES)}, {s: int(la[i]) for i, s in enumerate(STAGES)})
