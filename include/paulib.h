@@ -141,6 +141,41 @@ typedef void* (*paulib_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*paulib_free_fn)(void* ptr, void* stream, void* ctx);
 paulib_status paulib_set_allocator(paulib_alloc_fn alloc, paulib_free_fn free_, void* ctx);
 
+/* Canonical product of two small sums that allocates no memory (the paper
+ * has no counterpart; this is a service for callers that cannot allocate).
+ * Some callers cannot let a library call cudaMalloc: a process whose device
+ * memory is handed out by its own pool or fixed budget (an inference server
+ * that reserves all HBM at start-up, a control loop that must never enter
+ * the driver's allocator) would see a library allocation fail or break its
+ * budget.  This call computes exactly what paulib_multiply(...,
+ * PAULIB_FP64, PAULIB_OUT_CANONICAL, ...) computes, using only a fixed
+ * scratch area compiled into the library as a static device array of
+ * PAULIB_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads the library
+ * holds until the process exits.
+ *   Limits (PAULIB_ERR_UNSUPPORTED beyond them, before any device work):
+ *   n_qubits <= 256, na and nb <= 16384, na*nb <= 65536.
+ *   Inputs: device SoA arrays as in paulib_sum_create (word w of term t at
+ *   [w*n + t], complex128 coefficients), all phases zero.
+ *   Outputs: device arrays with room for out_capacity >= na*nb terms, SoA
+ *   with stride out_capacity (word w of output term t at
+ *   out_x[w*out_capacity + t]); *out_n (device int64) receives the number of
+ *   distinct strings; terms are in ascending key order.
+ *   The first call on a device looks up the scratch array's device address
+ *   (and sets kernel attributes); make that first call before any stream
+ *   capture on the device.  Every call shares the one scratch array, so
+ *   calls that overlap on the GPU (on different streams, or from different
+ *   host threads) race: serialise them.  Synchronises `stream` once, to
+ *   report device-side errors.                                             */
+#define PAULIB_NOALLOC_MAX_QUBITS 256
+#define PAULIB_NOALLOC_MAX_TERMS 16384
+#define PAULIB_NOALLOC_MAX_PRODUCTS 65536
+#define PAULIB_NOALLOC_SCRATCH_BYTES 8651008 /* about 8.25 MiB per GPU */
+paulib_status paulib_multiply_noalloc(int32_t n_qubits, int64_t na, const uint64_t* a_x,
+                                      const uint64_t* a_z, const double* a_c, int64_t nb,
+                                      const uint64_t* b_x, const uint64_t* b_z, const double* b_c,
+                                      uint64_t* out_x, uint64_t* out_z, double* out_c,
+                                      int64_t out_capacity, int64_t* out_n, void* stream);
+
 /* Diagnostics (no counterpart in the paper): device time of the library's
  * stages measured with CUDA events recorded on the launching stream, and the
  * number of kernels launched per stage.  Stages:

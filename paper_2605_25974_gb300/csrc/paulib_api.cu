@@ -408,6 +408,18 @@ paulib_status paulib_multiply_batched(int32_t batch, const paulib_sum* const* a,
     PAULIB_API_END
 }
 
+paulib_status paulib_multiply_noalloc(int32_t n_qubits, int64_t na, const uint64_t* a_x,
+                                      const uint64_t* a_z, const double* a_c, int64_t nb,
+                                      const uint64_t* b_x, const uint64_t* b_z, const double* b_c,
+                                      uint64_t* out_x, uint64_t* out_z, double* out_c,
+                                      int64_t out_capacity, int64_t* out_n, void* stream) {
+    PAULIB_API_BEGIN
+    multiply_noalloc(n_qubits, na, a_x, a_z, a_c, nb, b_x, b_z, b_c, out_x, out_z, out_c, out_capacity, out_n,
+                     (cudaStream_t)stream);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
 paulib_status paulib_timing_enable(int32_t on) {
     std::lock_guard<std::mutex> lk(g_t_mu);
     g_timing = on != 0;

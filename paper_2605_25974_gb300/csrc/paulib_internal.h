@@ -105,4 +105,11 @@ paulib_sum* canon_terms(const paulib_sum* in, int mode, cudaStream_t st);
 void canon_batched(int32_t batch, const paulib_sum* const* a, const paulib_sum* const* b, int mode,
                    cudaStream_t st, paulib_sum** out);
 
+// Allocation-free canonical product using the library's static scratch
+// array (see paulib_multiply_noalloc in include/paulib.h).
+void multiply_noalloc(int32_t n_qubits, int64_t na, const uint64_t* a_x, const uint64_t* a_z,
+                      const double* a_c, int64_t nb, const uint64_t* b_x, const uint64_t* b_z,
+                      const double* b_c, uint64_t* out_x, uint64_t* out_z, double* out_c,
+                      int64_t out_capacity, int64_t* out_n, cudaStream_t st);
+
 }  // namespace paulib

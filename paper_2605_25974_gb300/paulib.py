@@ -24,7 +24,8 @@ OUT_RAW, OUT_CANONICAL = 0, 1
 # Every symbol include/paulib.h declares.
 EXPORTED = ["paulib_abi_version", "paulib_sum_create", "paulib_sum_info", "paulib_sum_export",
             "paulib_sum_destroy", "paulib_multiply", "paulib_compress", "paulib_multiply_batched",
-            "paulib_last_error", "paulib_set_allocator", "paulib_timing_enable", "paulib_timing_read"]
+            "paulib_last_error", "paulib_set_allocator", "paulib_timing_enable", "paulib_timing_read",
+            "paulib_multiply_noalloc"]
 STAGES = ["convert", "sample", "count", "scatter", "level2", "compact", "raw", "export"]
 
 
