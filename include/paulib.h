@@ -130,6 +130,30 @@ paulib_status paulib_multiply_batched(int32_t batch, const paulib_sum* const* a,
                                       const paulib_sum* const* b, int32_t precision, void* stream,
                                       paulib_sum** out);
 
+/* Batched plan: the same batched canonical product, prepared once and then
+ * launched any number of times without allocating or synchronising, so a
+ * launch can be captured in a CUDA graph and replayed (e.g. one graph per
+ * Pauli-propagation step shape).  All problems are canonicalised together:
+ * the sort key is (problem index, string key), so one sample sort serves
+ * every problem and outputs come out grouped by problem.
+ *   create: validates the operands, sizes every buffer from |A_b|, |B_b| (each
+ *     output's capacity is |A_b|*|B_b|) and runs the product once to lay out
+ *     its workspace.  The operands must stay alive and unchanged while the
+ *     plan exists (a launch reads them again).
+ *   launch: enqueues the whole product on `stream` (kernels, device memsets
+ *     and device-to-device copies only).
+ *   outputs: synchronises `stream`, then fills out[batch] with handles to the
+ *     plan's output sums (canonical, owned by the plan, valid until the next
+ *     launch or destroy; do not destroy them).  Device errors of the last
+ *     launch are reported here.                                              */
+typedef struct paulib_batch_plan paulib_batch_plan;
+paulib_status paulib_batch_plan_create(int32_t batch, const paulib_sum* const* a,
+                                       const paulib_sum* const* b, int32_t precision, void* stream,
+                                       paulib_batch_plan** out);
+paulib_status paulib_batch_plan_launch(paulib_batch_plan* plan, void* stream);
+paulib_status paulib_batch_plan_outputs(paulib_batch_plan* plan, void* stream, paulib_sum** out);
+void paulib_batch_plan_destroy(paulib_batch_plan* plan);
+
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char* paulib_last_error(void);
 

@@ -45,8 +45,45 @@ static void configure_pool_once() {
     g_pool_configured[dev] = true;
 }
 
+namespace {
+struct ArenaState {
+    int mode = 0;  // 0 off, 1 recording, 2 replaying
+    char* base = nullptr;
+    size_t cap = 0, off = 0, total = 0;
+};
+thread_local ArenaState g_arena;
+constexpr size_t kArenaAlign = 256;
+}  // namespace
+
+void arena_record_begin() {
+    g_arena = ArenaState{};
+    g_arena.mode = 1;
+}
+size_t arena_record_end() {
+    const size_t t = g_arena.total;
+    g_arena = ArenaState{};
+    return t;
+}
+void arena_replay_begin(void* base, size_t bytes) {
+    g_arena = ArenaState{};
+    g_arena.mode = 2;
+    g_arena.base = static_cast<char*>(base);
+    g_arena.cap = bytes;
+}
+void arena_replay_end() { g_arena = ArenaState{}; }
+bool capture_safe() { return g_arena.mode == 2; }
+
 void* dev_alloc(size_t bytes, cudaStream_t s) {
     if (bytes == 0) return nullptr;
+    const size_t rounded = (bytes + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
+    if (g_arena.mode == 2) {
+        if (g_arena.off + rounded > g_arena.cap)
+            fail(PAULIB_ERR_INTERNAL, "plan workspace exhausted (launch does not match its recording)");
+        void* p = g_arena.base + g_arena.off;
+        g_arena.off += rounded;
+        return p;
+    }
+    if (g_arena.mode == 1) g_arena.total += rounded;
     if (g_alloc) {
         void* p = g_alloc(bytes, (void*)s, g_alloc_ctx);
         if (!p) fail(PAULIB_ERR_OOM, "allocator callback returned NULL for " + std::to_string(bytes) + " bytes");
@@ -63,7 +100,7 @@ void* dev_alloc(size_t bytes, cudaStream_t s) {
 }
 
 void dev_free(void* p, cudaStream_t s) {
-    if (!p) return;
+    if (!p || g_arena.mode == 2) return;
     if (g_free) { g_free(p, (void*)s, g_alloc_ctx); return; }
     cudaFreeAsync(p, s);
 }
@@ -121,7 +158,7 @@ StageScope::StageScope(int st, cudaStream_t str) : stage(st), s(str), outer(fals
     if (g_depth++ == 0) {
         outer = true;
         g_outer_stage = st;
-        if (g_timing) {
+        if (g_timing && !capture_safe()) {
             a = take_event();
             if (a && cudaEventRecord(a, s) != cudaSuccess) {
                 cudaGetLastError();
@@ -327,7 +364,7 @@ paulib_status paulib_sum_export(const paulib_sum* s, uint64_t* x_words, uint64_t
 }
 
 void paulib_sum_destroy(paulib_sum* s) {
-    if (!s) return;
+    if (!s || s->plan_owned) return;
     try {
         int cur = 0;
         cudaGetDevice(&cur);
@@ -406,6 +443,52 @@ paulib_status paulib_multiply_batched(int32_t batch, const paulib_sum* const* a,
     canon_batched(batch, a, b, precision, (cudaStream_t)stream, out);
     return PAULIB_OK;
     PAULIB_API_END
+}
+
+static void check_batch(int32_t batch, const paulib_sum* const* a, const paulib_sum* const* b) {
+    if (batch <= 0) fail(PAULIB_ERR_INVALID_ARG, "batch must be >= 1");
+    if (!a || !b) fail(PAULIB_ERR_INVALID_ARG, "NULL array argument");
+    for (int32_t i = 0; i < batch; ++i) {
+        check_pair(a[i], b[i]);
+        if (a[i]->n_qubits != a[0]->n_qubits)
+            fail(PAULIB_ERR_QUBIT_MISMATCH, "batched operands must share one qubit count");
+    }
+}
+
+paulib_status paulib_batch_plan_create(int32_t batch, const paulib_sum* const* a,
+                                       const paulib_sum* const* b, int32_t precision, void* stream,
+                                       paulib_batch_plan** out) {
+    if (out) *out = nullptr;
+    PAULIB_API_BEGIN
+    if (!out) fail(PAULIB_ERR_INVALID_ARG, "out is NULL");
+    check_mode(precision);
+    check_batch(batch, a, b);
+    *out = batch_plan_create(batch, a, b, precision, (cudaStream_t)stream);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_batch_plan_launch(paulib_batch_plan* plan, void* stream) {
+    PAULIB_API_BEGIN
+    if (!plan) fail(PAULIB_ERR_INVALID_ARG, "plan is NULL");
+    batch_plan_launch(plan, (cudaStream_t)stream);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_batch_plan_outputs(paulib_batch_plan* plan, void* stream, paulib_sum** out) {
+    PAULIB_API_BEGIN
+    if (!plan || !out) fail(PAULIB_ERR_INVALID_ARG, "NULL argument");
+    batch_plan_outputs(plan, (cudaStream_t)stream, out);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+void paulib_batch_plan_destroy(paulib_batch_plan* plan) {
+    try {
+        batch_plan_destroy(plan);
+    } catch (...) {
+    }
 }
 
 paulib_status paulib_multiply_noalloc(int32_t n_qubits, int64_t na, const uint64_t* a_x,

@@ -51,6 +51,13 @@ template <> __device__ __forceinline__ float2 one_v<float2>() { return make_floa
 // ---------------------------------------------------------------- record sources
 
 // Products of two sums: record r = j*na + i stands for a_i * b_j.
+//
+// When both operands are the same sum (sym != 0, e.g. H*H) only records with
+// i <= j exist.  P_a P_b and P_b P_a are the same string, and their phases
+// differ by 2*[a,b] (the symplectic inner product, Sec. III-D), so the pair
+// contributes i^k c_a c_b (1 + (-1)^[a,b]): twice one product when the
+// strings commute, exactly zero when they anti-commute.  The string is kept
+// either way, as in the ordered-pair form.
 template <int WP_, int MODE>
 struct ProdSrc {
     static constexpr int WP = WP_;
@@ -63,6 +70,7 @@ struct ProdSrc {
     const V* ac;
     const V* bc;
     uint32_t na;
+    uint32_t sym = 0;
     __device__ __forceinline__ void split(uint32_t r, uint32_t& i, uint32_t& j) const {
         j = r / na;
         i = r - j * na;
@@ -83,8 +91,46 @@ struct ProdSrc {
         uint64_t a[NW], b[NW];
         key_load_g<NW>(ak, i, a);
         key_load_g<NW>(bk, j, b);
-        const uint32_t ph = string_product<WP>(a, b, __ldg(ap + i), __ldg(bp + j), k);
-        return rot_v(mul_v(ac[i], bc[j]), ph);
+        const uint32_t ph = sym_flags(i, j, a, b) | string_product<WP>(a, b, __ldg(ap + i), __ldg(bp + j), k);
+        return apply(mul_v(ac[i], bc[j]), ph);
+    }
+    // Bit 2: the unordered pair cancels; bit 3: it counts twice.
+    __device__ __forceinline__ uint32_t sym_flags(uint32_t i, uint32_t j, const uint64_t (&a)[NW],
+                                                  const uint64_t (&b)[NW]) const {
+        if (!sym || i == j) return 0u;
+        uint64_t s = 0;
+#pragma unroll
+        for (int q = 0; q < WP; ++q) s ^= (a[q] & b[WP + q]) ^ (a[WP + q] & b[q]);
+        return (__popcll(s) & 1) ? 4u : 8u;
+    }
+    __device__ __forceinline__ V apply(V v, uint32_t ph) const {
+        if (ph & 4u) {
+            V z;
+            z.x = 0;
+            z.y = 0;
+            return z;
+        }
+        v = rot_v(v, ph & 3u);
+        if (ph & 8u) {
+            v.x += v.x;  // exact doubling
+            v.y += v.y;
+        }
+        return v;
+    }
+    // Product key and phase exponent (plus the symmetric-pair bits) only.
+    __device__ __forceinline__ uint32_t keyphase(uint32_t r, uint64_t (&k)[NW]) const {
+        uint32_t i, j;
+        split(r, i, j);
+        uint64_t a[NW], b[NW];
+        key_load_g<NW>(ak, i, a);
+        key_load_g<NW>(bk, j, b);
+        return sym_flags(i, j, a, b) | string_product<WP>(a, b, __ldg(ap + i), __ldg(bp + j), k);
+    }
+    // Coefficient of record r from its keyphase() bits.
+    __device__ __forceinline__ V coefv(uint32_t r, uint32_t ph) const {
+        uint32_t i, j;
+        split(r, i, j);
+        return apply(mul_v(ac[i], bc[j]), ph);
     }
 };
 
@@ -104,6 +150,33 @@ struct TermSrc {
         const V v = c ? c[r] : one_v<V>();
         return rot_v(v, phase ? (uint32_t)(__ldg(phase + r) & 3u) : 0u);
     }
+    __device__ __forceinline__ uint32_t keyphase(uint32_t r, uint64_t (&k)[NW]) const {
+        key_load_g<NW>(keys, r, k);
+        return phase ? (uint32_t)(__ldg(phase + r) & 3u) : 0u;
+    }
+    __device__ __forceinline__ V coefv(uint32_t r, uint32_t ph) const {
+        return rot_v(c ? c[r] : one_v<V>(), ph);
+    }
+};
+
+// Opaque NW-word keys with value 1 each: sorting them with the pipeline
+// yields the distinct keys and their multiplicities (used for splitters).
+template <int NW_>
+struct SampleSrc {
+    static constexpr int NW = NW_;
+    static constexpr int WP = NW_ / 2;
+    using V = double2;
+    const uint64_t* keys;
+    __device__ __forceinline__ void key(uint32_t r, uint64_t (&k)[NW]) const { key_load_g<NW>(keys, r, k); }
+    __device__ __forceinline__ V value(uint32_t r, uint64_t (&k)[NW]) const {
+        key_load_g<NW>(keys, r, k);
+        return make_double2(1.0, 0.0);
+    }
+    __device__ __forceinline__ uint32_t keyphase(uint32_t r, uint64_t (&k)[NW]) const {
+        key_load_g<NW>(keys, r, k);
+        return 0u;
+    }
+    __device__ __forceinline__ V coefv(uint32_t, uint32_t) const { return make_double2(1.0, 0.0); }
 };
 
 // ---------------------------------------------------------------- small helpers
@@ -127,6 +200,55 @@ __device__ __forceinline__ uint32_t upper_bound_keys(const uint64_t* spl, uint32
     while (len > 0) {
         const uint32_t half = len >> 1;
         if (key_cmp_m<NW>(k, spl + (uint64_t)(lo + half) * NW) >= 0) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo;
+}
+
+// Keys held in shared memory are stored word-major: word w of key t at
+// s[w * stride + t].  Lanes that touch different keys then touch different
+// banks; a key-major layout (32- or 64-byte records) puts every lane on the
+// same few banks.
+template <int NW>
+__device__ __forceinline__ void skey_store(uint64_t* s, uint32_t stride, uint32_t t, const uint64_t (&k)[NW]) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) s[(size_t)w * stride + t] = k[w];
+}
+template <int NW>
+__device__ __forceinline__ void skey_load(const uint64_t* s, uint32_t stride, uint32_t t, uint64_t (&k)[NW]) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) k[w] = s[(size_t)w * stride + t];
+}
+template <int NW>
+__device__ __forceinline__ int skey_cmp(const uint64_t* s, uint32_t stride, uint32_t a, uint32_t b) {
+#pragma unroll 4
+    for (int w = 0; w < NW; ++w) {
+        const uint64_t u = s[(size_t)w * stride + a], v = s[(size_t)w * stride + b];
+        if (u != v) return u < v ? -1 : 1;
+    }
+    return 0;
+}
+template <int NW>
+__device__ __forceinline__ int skey_cmp_r(const uint64_t (&k)[NW], const uint64_t* s, uint32_t stride, uint32_t b) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const uint64_t v = s[(size_t)w * stride + b];
+        if (k[w] != v) return k[w] < v ? -1 : 1;
+    }
+    return 0;
+}
+// Number of splitters <= k among n sorted word-major splitters.
+template <int NW>
+__device__ __forceinline__ uint32_t upper_bound_skeys(const uint64_t* s, uint32_t stride, uint32_t n,
+                                                      const uint64_t (&k)[NW]) {
+    uint32_t lo = 0, len = n;
+    while (len > 0) {
+        const uint32_t half = len >> 1;
+        if (skey_cmp_r<NW>(k, s, stride, lo + half) >= 0) {
             lo += half + 1;
             len -= half + 1;
         } else {
@@ -229,26 +351,37 @@ template <> struct Acc<M_F32_TWOSUM> {
 
 constexpr int kL2Threads = 512;
 constexpr int kStackCap = 4096;
-constexpr int kSmemBudget = 108 * 1024;
+constexpr int kSmemBudget = 110 * 1024;
 
-template <int NW, int VB>
+// Shared memory per leaf record: the product key (8*NW bytes), a packed sort
+// code (8 bytes), the record number (4 bytes, the tie-break that makes the
+// order of equal keys and so the summation order deterministic) and the
+// product's phase exponent (1 byte).  At most 4096 records, so a slot number
+// fits the code's low 12 bits.
+constexpr int kLeafRecBytes = 8 + 4 + 1;
+template <int NW>
 constexpr int leaf_cap() {
     int cap = 4096;
-    while (cap > 64 && cap * (8 * NW + VB + 6) > kSmemBudget) cap >>= 1;
+    while (cap > 64 && cap * (8 * NW + kLeafRecBytes) > kSmemBudget) cap >>= 1;
     return cap;
 }
-template <int NW, int VB>
+template <int NW>
 constexpr size_t leaf_smem() {
-    return (size_t)leaf_cap<NW, VB>() * (8 * NW + VB + 6);
+    return (size_t)leaf_cap<NW>() * (8 * NW + kLeafRecBytes);
 }
 
 // Coarse (level 1) splitters live in shared memory of the counting kernel.
 template <int NW>
 constexpr int max_coarse_splitters() {
-    return (64 * 1024) / (8 * NW) < 4094 ? (64 * 1024) / (8 * NW) : 4094;
+    return (128 * 1024) / (8 * NW) < 4094 ? (128 * 1024) / (8 * NW) : 4094;
 }
 
 // ---------------------------------------------------------------- sampling
+
+template <class Src>
+struct IsProdT : std::false_type {};
+template <int WP, int MODE>
+struct IsProdT<ProdSrc<WP, MODE>> : std::true_type {};
 
 template <class Src>
 __global__ void k_sample(Src src, uint32_t R, uint32_t S, uint64_t seed, uint64_t* out) {
@@ -257,6 +390,12 @@ __global__ void k_sample(Src src, uint32_t R, uint32_t S, uint64_t seed, uint64_
     uint32_t r;
     if (S >= R) r = s;
     else r = (uint32_t)(mix64(seed + s) % R);
+    if constexpr (IsProdT<Src>::value) {
+        if (src.sym) {  // fold onto the i <= j triangle
+            const uint32_t j = r / src.na, i = r - j * src.na;
+            if (i > j) r = i * src.na + j;
+        }
+    }
     uint64_t k[Src::NW];
     src.key(r, k);
     key_store<Src::NW>(out, s, k);
@@ -266,6 +405,24 @@ __global__ void k_sample(Src src, uint32_t R, uint32_t S, uint64_t seed, uint64_
 __global__ void k_iota(uint32_t* rec, uint32_t n, uint64_t* boff, uint8_t* bflags) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) rec[t] = t;
+    if (t == 0) {
+        boff[0] = 0;
+        boff[1] = n;
+        bflags[0] = 0;
+    }
+}
+
+// One coarse range holding the i <= j records of a symmetric product, in
+// order: t -> (i, j) with j(j+1)/2 <= t < (j+1)(j+2)/2.
+__global__ void k_iota_tri(uint32_t* rec, uint32_t n, uint32_t na, uint64_t* boff, uint8_t* bflags) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        uint64_t j = (uint64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while (j * (j + 1) / 2 > t) --j;
+        while ((j + 1) * (j + 2) / 2 <= t) ++j;
+        const uint64_t i = t - j * (j + 1) / 2;
+        rec[t] = (uint32_t)(j * na + i);
+    }
     if (t == 0) {
         boff[0] = 0;
         boff[1] = n;
@@ -343,7 +500,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count_prod(ProdSrc<WP, MODE> 
     uint64_t* s_b = s_spl + (size_t)nsp * NW;
     uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_b + kCountCols * NW);
     const uint32_t nbk = nsp + 1;
-    for (uint32_t q = threadIdx.x; q < nsp * NW; q += blockDim.x) s_spl[q] = spl[q];
+    for (uint32_t q = threadIdx.x; q < nsp * NW; q += blockDim.x) s_spl[(q % NW) * nsp + q / NW] = spl[q];
     for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x) s_hist[q] = 0;
     const uint32_t na = src.na;
     const uint32_t ti_n = (na + kCountThreads - 1) / kCountThreads;
@@ -361,11 +518,12 @@ __global__ void __launch_bounds__(kCountThreads) k_count_prod(ProdSrc<WP, MODE> 
             uint64_t a[NW];
             key_load_g<NW>(src.ak, i, a);
             for (uint32_t c = 0; c < ncols; ++c) {
+                if (src.sym && i > j0 + c) continue;  // the (j, i) record stands for both orders
                 uint64_t k[NW];
                 const uint64_t* bb = s_b + c * NW;
 #pragma unroll
                 for (int q = 0; q < NW; ++q) k[q] = a[q] ^ bb[q];
-                const uint32_t bkt = upper_bound_keys<NW>(s_spl, nsp, k);
+                const uint32_t bkt = upper_bound_skeys<NW>(s_spl, nsp, nsp, k);
                 ids[(uint64_t)(j0 + c) * na + i] = (uint16_t)bkt;
                 atomicAdd(&s_hist[bkt], 1u);
             }
@@ -386,13 +544,13 @@ __global__ void __launch_bounds__(kCountThreads) k_count_lin(Src src, uint32_t R
     uint64_t* s_spl = reinterpret_cast<uint64_t*>(smem);
     uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_spl + (size_t)nsp * NW);
     const uint32_t nbk = nsp + 1;
-    for (uint32_t q = threadIdx.x; q < nsp * NW; q += blockDim.x) s_spl[q] = spl[q];
+    for (uint32_t q = threadIdx.x; q < nsp * NW; q += blockDim.x) s_spl[(q % NW) * nsp + q / NW] = spl[q];
     for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x) s_hist[q] = 0;
     __syncthreads();
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
         uint64_t k[NW];
         src.key(r, k);
-        const uint32_t bkt = upper_bound_keys<NW>(s_spl, nsp, k);
+        const uint32_t bkt = upper_bound_skeys<NW>(s_spl, nsp, nsp, k);
         ids[r] = (uint16_t)bkt;
         atomicAdd(&s_hist[bkt], 1u);
     }
@@ -453,7 +611,7 @@ constexpr uint32_t kScatterChunk = 32768;
 
 __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint16_t* __restrict__ ids, uint32_t R,
                                                              uint32_t nbk, uint64_t* cursor,
-                                                             uint32_t* rec) {
+                                                             uint32_t* rec, uint32_t sym_na) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);
     uint64_t* s_base = reinterpret_cast<uint64_t*>(s_cnt + ((nbk + 1) & ~1u));
@@ -462,7 +620,10 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint16_t* __r
         __syncthreads();
         for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x) s_cnt[q] = 0;
         __syncthreads();
-        for (uint32_t r = (uint32_t)c0 + threadIdx.x; r < c1; r += blockDim.x) atomicAdd(&s_cnt[ids[r]], 1u);
+        for (uint32_t r = (uint32_t)c0 + threadIdx.x; r < c1; r += blockDim.x) {
+            if (sym_na && r % sym_na > r / sym_na) continue;  // no record for i > j
+            atomicAdd(&s_cnt[ids[r]], 1u);
+        }
         __syncthreads();
         for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x) {
             const uint32_t c = s_cnt[q];
@@ -471,6 +632,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint16_t* __r
         }
         __syncthreads();
         for (uint32_t r = (uint32_t)c0 + threadIdx.x; r < c1; r += blockDim.x) {
+            if (sym_na && r % sym_na > r / sym_na) continue;
             const uint32_t b = ids[r];
             const uint32_t p = atomicAdd(&s_cnt[b], 1u);
             rec[s_base[b] + p] = r;
@@ -483,15 +645,105 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint16_t* __r
 struct StackEnt {
     uint32_t lo, hi, flags, pad;
 };
+enum : uint32_t { SF_UNIFORM = 1u, SF_INB = 2u };
 
 template <class Src, int MODE>
 struct L2Cfg {
     using V = typename Src::V;
     static constexpr int NW = Src::NW;
-    static constexpr int VB = (int)sizeof(V);
-    static constexpr int CAP = leaf_cap<NW, VB>();
-    static constexpr size_t SMEM = leaf_smem<NW, VB>();
+    static constexpr int CAP = leaf_cap<NW>();
+    static constexpr size_t SMEM = leaf_smem<NW>();
 };
+
+// Order of two packed sort codes.  A code holds, above bit 12, the 52 key
+// bits that follow the common prefix of every key in the range, and the
+// element's slot below.  Equal upper bits fall back to the full keys, then to
+// the record number; slots >= n are padding that sorts last.
+template <int NW, uint32_t CAP>
+__device__ __forceinline__ bool code_gt(uint64_t a, uint64_t b, const uint64_t* keys_s, uint32_t n,
+                                        const uint32_t* recs, uint32_t lo) {
+    if ((a ^ b) >> 12) return a > b;
+    const uint32_t ia = (uint32_t)(a & 0xFFFu), ib = (uint32_t)(b & 0xFFFu);
+    if (ia >= n || ib >= n) return ia >= n && (ib < n || ia > ib);
+    const int c = skey_cmp<NW>(keys_s, CAP, ia, ib);
+    if (c) return c > 0;
+    if (recs) return recs[ia] > recs[ib];
+    return ia > ib;
+}
+
+template <int NW, uint32_t CAP>
+__device__ __forceinline__ bool code_key_neq(uint64_t a, uint64_t b, const uint64_t* keys_s) {
+    if ((a ^ b) >> 12) return true;
+    return skey_cmp<NW>(keys_s, CAP, (uint32_t)(a & 0xFFFu), (uint32_t)(b & 0xFFFu)) != 0;
+}
+
+// Packed codes for keys_s[0..n): the first bit position L where any key
+// differs from key 0 is found with an OR reduction; each code then takes the
+// 52 bits starting at L.  Slots [n, p2) get padding codes.
+template <int NW, int T, uint32_t CAP>
+__device__ void build_codes(uint64_t* code_s, const uint64_t* keys_s, uint32_t n, uint32_t p2,
+                            unsigned long long* s_or, uint32_t* s_L) {
+    for (int w = threadIdx.x; w < NW; w += T) s_or[w] = 0ull;
+    __syncthreads();
+    uint64_t acc[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) acc[w] = 0;
+    for (uint32_t t = threadIdx.x; t < n; t += T) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) acc[w] |= keys_s[(size_t)w * CAP + t] ^ keys_s[(size_t)w * CAP];
+    }
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        uint64_t v = acc[w];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicOr(&s_or[w], (unsigned long long)v);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t L = 64u * NW;
+        for (int w = 0; w < NW; ++w)
+            if (s_or[w]) { L = 64u * w + (uint32_t)__clzll((long long)s_or[w]); break; }
+        *s_L = L;
+    }
+    __syncthreads();
+    const uint32_t L = *s_L;
+    const uint32_t w0 = L >> 6, sh = L & 63u;
+    for (uint32_t t = threadIdx.x; t < p2; t += T) {
+        uint64_t code;
+        if (t >= n) {
+            code = ~0xFFFull | t;
+        } else if (w0 >= (uint32_t)NW) {
+            code = t;
+        } else {
+            uint64_t hi = keys_s[(size_t)w0 * CAP + t] << sh;
+            if (sh && w0 + 1 < (uint32_t)NW) hi |= keys_s[(size_t)(w0 + 1) * CAP + t] >> (64u - sh);
+            code = (hi & ~0xFFFull) | t;
+        }
+        code_s[t] = code;
+    }
+    __syncthreads();
+}
+
+template <int NW, int T, uint32_t CAP>
+__device__ void block_sort_codes(uint64_t* code_s, const uint64_t* keys_s, uint32_t n, uint32_t p2,
+                                 const uint32_t* recs, uint32_t lo) {
+    for (uint32_t kk = 2; kk <= p2; kk <<= 1) {
+        for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (uint32_t t = threadIdx.x; t < p2 / 2; t += T) {
+                const uint32_t i = 2 * t - (t & (jj - 1));
+                const uint32_t l = i + jj;
+                const uint64_t a = code_s[i], b = code_s[l];
+                const bool up = (i & kk) == 0;
+                if (code_gt<NW, CAP>(a, b, keys_s, n, recs, lo) == up) {
+                    code_s[i] = b;
+                    code_s[l] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
 
 template <class Src, int MODE>
 __global__ void __launch_bounds__(kL2Threads) k_level2(
@@ -499,18 +751,17 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
     uint32_t* recA, uint32_t* recB, uint16_t* subid, uint32_t* ticket, StackEnt* stacks,
     uint64_t* spl_scratch, uint64_t* Tkeys, double2* Tcoef, uint64_t* ucount, int32_t* err) {
     using Cfg = L2Cfg<Src, MODE>;
-    using V = typename Cfg::V;
     constexpr int NW = Cfg::NW;
     constexpr uint32_t CAP = Cfg::CAP;
     constexpr int T = kL2Threads;
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* keys_s = reinterpret_cast<uint64_t*>(smem);
-    V* val_s = reinterpret_cast<V*>(keys_s + (size_t)CAP * NW);
-    uint32_t* rec_s = reinterpret_cast<uint32_t*>(val_s + CAP);
-    uint16_t* perm_s = reinterpret_cast<uint16_t*>(rec_s + CAP);
-    uint8_t* ufl_s = reinterpret_cast<uint8_t*>(perm_s);  // reused during splits
+    uint64_t* keys_s = reinterpret_cast<uint64_t*>(smem);                     // [NW][CAP]
+    uint64_t* code_s = keys_s + (size_t)CAP * NW;                             // [CAP]
+    uint32_t* rec_s = reinterpret_cast<uint32_t*>(code_s + CAP);              // [CAP]
+    uint8_t* ph_s = reinterpret_cast<uint8_t*>(rec_s + CAP);                  // [CAP]
     __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_bucket, s_lo, s_hi, s_fl, s_sp, s_done, s_nsp, s_bad;
+    __shared__ unsigned long long s_or[NW];
+    __shared__ uint32_t s_bucket, s_lo, s_hi, s_fl, s_sp, s_done, s_nsp, s_bad, s_L;
     __shared__ uint64_t s_u, s_tbase;
 
     StackEnt* stack = stacks + (size_t)blockIdx.x * kStackCap;
@@ -530,7 +781,7 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
             s_bad = 0;
             s_sp = 0;
             if (end0 > base0) {
-                stack[0] = StackEnt{(uint32_t)base0, (uint32_t)end0, (uint32_t)bflags[c], 0u};
+                stack[0] = StackEnt{(uint32_t)base0, (uint32_t)end0, bflags[c] ? SF_UNIFORM : 0u, 0u};
                 s_sp = 1;
             }
         }
@@ -558,17 +809,19 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
             const uint32_t lo = s_lo, hi = s_hi, fl = s_fl;
             const uint32_t n = hi - lo;
             const uint64_t tout = s_tbase + s_u;
+            uint32_t* cur = (fl & SF_INB) ? recB : recA;
+            uint32_t* oth = (fl & SF_INB) ? recA : recB;
 
-            if (fl & 1u) {
-                // ---- uniform range: every record has the same key
+            if (fl & SF_UNIFORM) {
+                // ---- every record in the range has the same key
                 Acc<MODE> acc;
                 for (uint32_t t = tid; t < n; t += T) {
                     uint64_t k[NW];
-                    acc.add(src.value(recA[lo + t], k));
+                    acc.add(src.value(cur[lo + t], k));
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc.shfl_merge(o);
-                Acc<MODE>* s_acc = reinterpret_cast<Acc<MODE>*>(val_s);
+                Acc<MODE>* s_acc = reinterpret_cast<Acc<MODE>*>(code_s);
                 if ((tid & 31) == 0) s_acc[tid >> 5] = acc;
                 __syncthreads();
                 if (tid < 32) {
@@ -578,7 +831,7 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
                     for (int o = 16; o > 0; o >>= 1) a2.shfl_merge(o);
                     if (tid == 0) {
                         uint64_t k[NW];
-                        src.key(recA[lo], k);
+                        src.key(cur[lo], k);
                         key_store<NW>(Tkeys, tout, k);
                         Tcoef[tout] = a2.result();
                         s_u += 1;
@@ -586,64 +839,40 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
                 }
                 __syncthreads();
             } else if (n <= CAP) {
-                // ---- leaf: gather, sort by (key, record), merge equal runs
+                // ---- leaf: product keys and phases into shared memory, sort
+                // by (key, record), then sum each run of equal keys
                 for (uint32_t t = tid; t < n; t += T) {
-                    const uint32_t r = recA[lo + t];
                     uint64_t k[NW];
-                    const V v = src.value(r, k);
-                    key_store<NW>(keys_s, t, k);
-                    val_s[t] = v;
+                    const uint32_t r = cur[lo + t];
                     rec_s[t] = r;
+                    ph_s[t] = (uint8_t)src.keyphase(r, k);
+                    skey_store<NW>(keys_s, CAP, t, k);
                 }
                 uint32_t p2 = 1;
                 while (p2 < n) p2 <<= 1;
-                for (uint32_t t = tid; t < p2; t += T) perm_s[t] = (uint16_t)t;
                 __syncthreads();
-                for (uint32_t kk = 2; kk <= p2; kk <<= 1) {
-                    for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
-                        for (uint32_t t = tid; t < p2 / 2; t += T) {
-                            const uint32_t i = 2 * t - (t & (jj - 1));
-                            const uint32_t l = i + jj;
-                            const uint32_t pa = perm_s[i], pb = perm_s[l];
-                            bool gt;  // element pa sorts after element pb
-                            if (pa >= n) gt = pb < n;
-                            else if (pb >= n) gt = false;
-                            else {
-                                const int cm = key_cmp_mm<NW>(keys_s + (size_t)pa * NW, keys_s + (size_t)pb * NW);
-                                gt = cm > 0 || (cm == 0 && rec_s[pa] > rec_s[pb]);
-                            }
-                            const bool up = (i & kk) == 0;
-                            if (gt == up) {
-                                perm_s[i] = (uint16_t)pb;
-                                perm_s[l] = (uint16_t)pa;
-                            }
-                        }
-                        __syncthreads();
-                    }
-                }
-                // heads: position p starts a run if its key differs from p-1
+                build_codes<NW, T, CAP>(code_s, keys_s, n, p2, s_or, &s_L);
+                block_sort_codes<NW, T, CAP>(code_s, keys_s, n, p2, rec_s, 0);
                 constexpr uint32_t IPT = (CAP + T - 1) / T;
                 const uint32_t p0 = tid * IPT;
+                const uint32_t p1 = min(n, p0 + IPT);
                 uint32_t my_heads = 0;
-                for (uint32_t p = p0; p < min(n, p0 + IPT); ++p) {
-                    if (p == 0 || key_cmp_mm<NW>(keys_s + (size_t)perm_s[p] * NW,
-                                                 keys_s + (size_t)perm_s[p - 1] * NW) != 0)
-                        ++my_heads;
-                }
+                for (uint32_t p = p0; p < p1; ++p)
+                    if (p == 0 || code_key_neq<NW, CAP>(code_s[p], code_s[p - 1], keys_s)) ++my_heads;
                 uint32_t total;
                 uint32_t hidx = block_excl_scan<T>(my_heads, s_warp, total);
-                for (uint32_t p = p0; p < min(n, p0 + IPT); ++p) {
-                    const uint64_t* kp = keys_s + (size_t)perm_s[p] * NW;
-                    if (p == 0 || key_cmp_mm<NW>(kp, keys_s + (size_t)perm_s[p - 1] * NW) != 0) {
+                for (uint32_t p = p0; p < p1; ++p) {
+                    const uint64_t hc = code_s[p];
+                    if (p == 0 || code_key_neq<NW, CAP>(hc, code_s[p - 1], keys_s)) {
                         Acc<MODE> acc;
-                        acc.add(val_s[perm_s[p]]);
-                        uint32_t q = p + 1;
-                        while (q < n && key_cmp_mm<NW>(kp, keys_s + (size_t)perm_s[q] * NW) == 0) {
-                            acc.add(val_s[perm_s[q]]);
+                        uint32_t q = p;
+                        do {
+                            const uint32_t idx = (uint32_t)(code_s[q] & 0xFFFu);
+                            acc.add(src.coefv(rec_s[idx], ph_s[idx]));
                             ++q;
-                        }
+                        } while (q < n && !code_key_neq<NW, CAP>(hc, code_s[q], keys_s));
                         uint64_t k[NW];
-                        key_load_s<NW>(keys_s, perm_s[p], k);
+                        skey_load<NW>(keys_s, CAP, (uint32_t)(hc & 0xFFFu), k);
                         key_store<NW>(Tkeys, tout + hidx, k);
                         Tcoef[tout + hidx] = acc.result();
                         ++hidx;
@@ -653,58 +882,40 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
                 if (tid == 0) s_u += total;
                 __syncthreads();
             } else {
-                // ---- split: splitters from a sample of this range
+                // ---- split: splitters from a sorted sample of this range
                 const uint32_t S = CAP;
                 for (uint32_t t = tid; t < S; t += T) {
                     const uint32_t pos = lo + (uint32_t)(((uint64_t)t * n) / S);
                     uint64_t k[NW];
-                    src.key(recA[pos], k);
-                    key_store<NW>(keys_s, t, k);
-                    rec_s[t] = t;
-                    perm_s[t] = (uint16_t)t;
+                    src.key(cur[pos], k);
+                    skey_store<NW>(keys_s, CAP, t, k);
                 }
                 __syncthreads();
-                for (uint32_t kk = 2; kk <= S; kk <<= 1) {
-                    for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
-                        for (uint32_t t = tid; t < S / 2; t += T) {
-                            const uint32_t i = 2 * t - (t & (jj - 1));
-                            const uint32_t l = i + jj;
-                            const uint32_t pa = perm_s[i], pb = perm_s[l];
-                            const int cm = key_cmp_mm<NW>(keys_s + (size_t)pa * NW, keys_s + (size_t)pb * NW);
-                            const bool gt = cm > 0 || (cm == 0 && pa > pb);
-                            const bool up = (i & kk) == 0;
-                            if (gt == up) {
-                                perm_s[i] = (uint16_t)pb;
-                                perm_s[l] = (uint16_t)pa;
-                            }
-                        }
-                        __syncthreads();
-                    }
-                }
+                build_codes<NW, T, CAP>(code_s, keys_s, S, S, s_or, &s_L);
+                block_sort_codes<NW, T, CAP>(code_s, keys_s, S, S, nullptr, 0);
                 const uint32_t want = (uint32_t)mn<uint64_t>(CAP / 4, ((uint64_t)n + CAP / 2 - 1) / (CAP / 2));
+                uint8_t* fl_s = ph_s;  // flag of range b+1 follows splitter b
                 if (tid == 0) {
                     uint32_t nsp = 0;
-                    // bucket m+1 follows splitter m; flags staged in rec_s[CAP/2 ..]
-                    uint32_t* fl_tmp = rec_s + CAP / 2;
-                    fl_tmp[0] = 0;
+                    fl_s[0] = 0;
                     bool stop = false;
                     for (uint32_t t = 1; t < want && !stop; ++t) {
                         const uint32_t rho = (uint32_t)(((uint64_t)t * S) / want);
-                        const uint64_t* cand = keys_s + (size_t)perm_s[rho] * NW;
-                        if (nsp > 0 && key_cmp_mm<NW>(cand, my_spl + (size_t)(nsp - 1) * NW) <= 0) continue;
-                        const bool heavy =
-                            (rho > 0 && key_cmp_mm<NW>(cand, keys_s + (size_t)perm_s[rho - 1] * NW) == 0) ||
-                            (rho + 1 < S && key_cmp_mm<NW>(cand, keys_s + (size_t)perm_s[rho + 1] * NW) == 0);
+                        const uint32_t ci = (uint32_t)(code_s[rho] & 0xFFFu);
                         uint64_t k[NW], s2[NW];
-                        for (int q = 0; q < NW; ++q) k[q] = cand[q];
+                        skey_load<NW>(keys_s, CAP, ci, k);
+                        if (nsp > 0 && key_cmp_m<NW>(k, my_spl + (size_t)(nsp - 1) * NW) <= 0) continue;
+                        const bool heavy =
+                            (rho > 0 && skey_cmp<NW>(keys_s, CAP, ci, (uint32_t)(code_s[rho - 1] & 0xFFFu)) == 0) ||
+                            (rho + 1 < S && skey_cmp<NW>(keys_s, CAP, ci, (uint32_t)(code_s[rho + 1] & 0xFFFu)) == 0);
                         key_store<NW>(my_spl, nsp, k);
                         ++nsp;
-                        fl_tmp[nsp] = heavy ? 1u : 0u;
+                        fl_s[nsp] = heavy ? 1u : 0u;
                         if (heavy) {
                             if (key_succ<NW>(k, s2)) {
                                 key_store<NW>(my_spl, nsp, s2);
                                 ++nsp;
-                                fl_tmp[nsp] = 0;
+                                fl_s[nsp] = 0;
                             } else {
                                 stop = true;  // nothing sorts after the largest key
                             }
@@ -715,18 +926,15 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
                 __syncthreads();
                 const uint32_t nsp = s_nsp;
                 const uint32_t nbs = nsp + 1;
-                // splitters into shared memory; flags into ufl_s; counters in rec_s
-                for (uint32_t q = tid; q < nsp * NW; q += T) keys_s[q] = my_spl[q];
-                for (uint32_t q = tid; q < nbs; q += T) ufl_s[q] = (uint8_t)rec_s[CAP / 2 + q];
-                __syncthreads();
-                uint32_t* cnt = rec_s;                 // [nbs]
-                uint32_t* cur = rec_s + CAP / 2;       // [nbs]  (nbs <= CAP/2)
-                for (uint32_t q = tid; q < nbs; q += T) { cnt[q] = 0; cur[q] = 0; }
+                for (uint32_t q = tid; q < nsp * NW; q += T) keys_s[(q % NW) * (CAP / 2) + q / NW] = my_spl[q];
+                uint32_t* cnt = reinterpret_cast<uint32_t*>(code_s);  // [nbs]
+                uint32_t* cpos = cnt + CAP / 2;                         // [nbs]
+                for (uint32_t q = tid; q < nbs; q += T) { cnt[q] = 0; cpos[q] = 0; }
                 __syncthreads();
                 for (uint32_t idx = lo + tid; idx < hi; idx += T) {
                     uint64_t k[NW];
-                    src.key(recA[idx], k);
-                    const uint32_t b = upper_bound_keys<NW>(keys_s, nsp, k);
+                    src.key(cur[idx], k);
+                    const uint32_t b = upper_bound_skeys<NW>(keys_s, CAP / 2, nsp, k);
                     subid[idx] = (uint16_t)b;
                     atomicAdd(&cnt[b], 1u);
                 }
@@ -736,7 +944,7 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
                     uint32_t bad = 0;
                     for (uint32_t b = 0; b < nbs; ++b) {
                         const uint32_t cb = cnt[b];
-                        if (cb == n && !(ufl_s[b] & 1u)) bad = 1;  // no progress
+                        if (cb == n && !(fl_s[b] & 1u)) bad = 1;  // no progress
                         cnt[b] = run;
                         run += cb;
                     }
@@ -747,18 +955,17 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
                 if (!s_bad) {
                     for (uint32_t idx = lo + tid; idx < hi; idx += T) {
                         const uint32_t b = subid[idx];
-                        const uint32_t p = atomicAdd(&cur[b], 1u);
-                        recB[lo + cnt[b] + p] = recA[idx];
+                        const uint32_t p = atomicAdd(&cpos[b], 1u);
+                        oth[lo + cnt[b] + p] = cur[idx];
                     }
                     __syncthreads();
-                    for (uint32_t idx = lo + tid; idx < hi; idx += T) recA[idx] = recB[idx];
-                    __syncthreads();
                     if (tid == 0) {
-                        // push in reverse so the smallest keys are popped first
+                        const uint32_t inb = (fl & SF_INB) ? 0u : SF_INB;  // children live in the other buffer
                         for (int b = (int)nbs - 1; b >= 0; --b) {
                             const uint32_t s0 = cnt[b];
                             const uint32_t s1 = (b + 1 < (int)nbs) ? cnt[b + 1] : n;
-                            if (s1 > s0) stack[s_sp++] = StackEnt{lo + s0, lo + s1, (uint32_t)(ufl_s[b] & 1u), 0u};
+                            if (s1 > s0)
+                                stack[s_sp++] = StackEnt{lo + s0, lo + s1, ((fl_s[b] & 1u) ? SF_UNIFORM : 0u) | inb, 0u};
                         }
                     }
                 }
@@ -820,6 +1027,18 @@ __global__ void k_to_f32(const double2* __restrict__ in, float2* out, int64_t n)
 
 // ---------------------------------------------------------------- host pipeline
 
+// Opt a kernel into more than 48 KB of dynamic shared memory.  Attributes
+// persist, so a capture-safe (replayed) launch skips the call.
+template <class F>
+static void smem_attr(F* kern, size_t bytes) {
+    if (capture_safe()) return;
+    check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes), "attr");
+}
+
+__global__ void k_or_err(const int32_t* inner, int32_t* outer) {
+    if (threadIdx.x == 0 && *inner) atomicOr(outer, *inner);
+}
+
 struct Staged {
     // merged terms of every coarse range, dense within [boff[c], boff[c] + U_c)
     Scratch Tkeys, Tcoef, boff, uoff, err;
@@ -837,13 +1056,12 @@ template <class Src, int MODE>
 static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStream_t st, Staged& out);
 
 // Sorted distinct sample keys with their multiplicities.
-template <int WP>
+template <int NW>
 static void sorted_sample(const uint64_t* samp, uint32_t S, cudaStream_t st, Scratch& dk, Scratch& dc,
-                          Scratch& du) {
-    constexpr int NW = 2 * WP;
-    TermSrc<WP, M_FP64> ts{samp, nullptr, nullptr};
+                          Scratch& du, int32_t* outer_err) {
+    SampleSrc<NW> ts{samp};
     Staged sg;
-    run_pipeline<TermSrc<WP, M_FP64>, M_FP64>(ts, S, 0, st, sg);
+    run_pipeline<SampleSrc<NW>, M_FP64>(ts, S, 0, st, sg);
     dk = Scratch((size_t)S * NW * 8, st);
     dc = Scratch((size_t)S * 16, st);
     du = Scratch(8, st);
@@ -854,12 +1072,9 @@ static void sorted_sample(const uint64_t* samp, uint32_t S, cudaStream_t st, Scr
     check_cuda(cudaMemcpyAsync(du.p, sg.uoff.as<uint64_t>() + sg.nbk, 8, cudaMemcpyDeviceToDevice, st),
                "sample count copy");
     check_cuda(cudaGetLastError(), "sample compaction");
-    // errors of the inner pipeline are folded into the caller's error word by
-    // the caller reading `sg.err` is not possible after return; surface them now
-    int32_t e = 0;
-    check_cuda(cudaMemcpyAsync(&e, sg.err.p, 4, cudaMemcpyDeviceToHost, st), "err copy");
-    check_cuda(cudaStreamSynchronize(st), "sample sync");
-    if (e) fail(PAULIB_ERR_INTERNAL, "splitter sample sort failed (device error " + std::to_string(e) + ")");
+    // the inner pipeline's error word joins the caller's (no host sync)
+    k_or_err<<<1, 32, 0, st>>>(sg.err.as<int32_t>(), outer_err);
+    check_cuda(cudaGetLastError(), "k_or_err");
 }
 
 template <class Src, int MODE>
@@ -872,23 +1087,36 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
 
     out.err = Scratch(4, st);
     check_cuda(cudaMemsetAsync(out.err.p, 0, 4, st), "memset err");
-    Scratch recA((size_t)R * 4, st), recB((size_t)R * 4, st), subid((size_t)R * 2, st);
+    // R indexes the record space; Reff records exist (fewer for a symmetric product)
+    uint32_t sym_na = 0;
+    uint64_t Reff = R;
+    if constexpr (IsProd<Src>::value) {
+        if (src.sym) {
+            sym_na = src.na;
+            Reff = (uint64_t)src.na * (src.na + 1) / 2;
+        }
+    }
+    Scratch recA((size_t)Reff * 4, st), recB((size_t)Reff * 4, st), subid((size_t)R * 2, st);
     Scratch bflags_s, cnt_s;
     uint32_t nbk = 1;
     const uint64_t C1 = (uint64_t)CAP * 16;
 
-    if ((uint64_t)R <= C1) {
+    if (Reff <= C1) {
         StageScope ss(ST_SCATTER, st);
         out.boff = Scratch(16, st);
         bflags_s = Scratch(1, st);
-        k_iota<<<(R + 255) / 256, 256, 0, st>>>(recA.as<uint32_t>(), R, out.boff.as<uint64_t>(),
-                                                bflags_s.as<uint8_t>());
+        if (sym_na)
+            k_iota_tri<<<(unsigned)((Reff + 255) / 256), 256, 0, st>>>(recA.as<uint32_t>(), (uint32_t)Reff, sym_na,
+                                                                     out.boff.as<uint64_t>(), bflags_s.as<uint8_t>());
+        else
+            k_iota<<<(R + 255) / 256, 256, 0, st>>>(recA.as<uint32_t>(), R, out.boff.as<uint64_t>(),
+                                                    bflags_s.as<uint8_t>());
         note_launch(ST_SCATTER);
         check_cuda(cudaGetLastError(), "k_iota");
     } else {
         const uint32_t bmax = (uint32_t)(max_coarse_splitters<NW>() / 2 + 1);
-        const uint32_t B1 = (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>(bmax, (R + C1 - 1) / C1));
-        const uint32_t S = (uint32_t)std::min<uint64_t>(R, (uint64_t)B1 * 32);
+        const uint32_t B1 = (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>(bmax, (Reff + C1 - 1) / C1));
+        const uint32_t S = (uint32_t)std::min<uint64_t>(Reff, (uint64_t)B1 * 32);
         Scratch samp((size_t)S * NW * 8, st);
         const uint32_t nsp = 2 * (B1 - 1);
         nbk = nsp + 1;
@@ -900,7 +1128,7 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
             note_launch(ST_SAMPLE);
             check_cuda(cudaGetLastError(), "k_sample");
             Scratch dk, dc, du;
-            sorted_sample<WP>(samp.as<uint64_t>(), S, st, dk, dc, du);
+            sorted_sample<NW>(samp.as<uint64_t>(), S, st, dk, dc, du, out.err.as<int32_t>());
             k_select<NW><<<1, 1024, 0, st>>>(dk.as<uint64_t>(), dc.as<double2>(), du.as<uint64_t>(), S, B1,
                                              pref.as<uint32_t>(), spl.as<uint64_t>(), bflags_s.as<uint8_t>());
             note_launch(ST_SAMPLE);
@@ -913,7 +1141,7 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
         if constexpr (IsProd<Src>::value) {
             const size_t sm = (size_t)nsp * NW * 8 + (size_t)kCountCols * NW * 8 + (size_t)nbk * 4;
             auto kern = k_count_prod<WP, MODE>;
-            check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), "attr");
+            smem_attr(kern, sm);
             const uint64_t tiles = (uint64_t)((src.na + kCountThreads - 1) / kCountThreads) *
                                    ((nb_terms + kCountCols - 1) / kCountCols);
             const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)sms * 4));
@@ -922,7 +1150,7 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
         } else {
             const size_t sm = (size_t)nsp * NW * 8 + (size_t)nbk * 4;
             auto kern = k_count_lin<Src>;
-            check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), "attr");
+            smem_attr(kern, sm);
             const unsigned grid = (unsigned)std::max<uint64_t>(
                 1, std::min<uint64_t>(((uint64_t)R + kCountThreads - 1) / kCountThreads, (uint64_t)sms * 4));
             kern<<<grid, kCountThreads, sm, st>>>(src, R, spl.as<uint64_t>(), nsp, subid.as<uint16_t>(),
@@ -938,26 +1166,26 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
         Scratch cursor((size_t)nbk * 8, st);
         check_cuda(cudaMemcpyAsync(cursor.p, out.boff.p, (size_t)nbk * 8, cudaMemcpyDeviceToDevice, st), "cursor");
         const size_t sm = (size_t)((nbk + 1) & ~1u) * 4 + (size_t)nbk * 8;
-        check_cuda(cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), "attr");
+        smem_attr(k_scatter, sm);
         const unsigned grid = (unsigned)std::max<uint64_t>(
             1, std::min<uint64_t>(((uint64_t)R + kScatterChunk - 1) / kScatterChunk, (uint64_t)sms * 2));
         k_scatter<<<grid, kScatterThreads, sm, st>>>(subid.as<uint16_t>(), R, nbk, cursor.as<uint64_t>(),
-                                                    recA.as<uint32_t>());
+                                                    recA.as<uint32_t>(), sym_na);
         note_launch(ST_SCATTER);
         check_cuda(cudaGetLastError(), "k_scatter");
     }
 
     // level 2
     out.nbk = nbk;
-    out.Tkeys = Scratch((size_t)R * NW * 8, st);
-    out.Tcoef = Scratch((size_t)R * 16, st);
+    out.Tkeys = Scratch((size_t)Reff * NW * 8, st);
+    out.Tcoef = Scratch((size_t)Reff * 16, st);
     Scratch ucount((size_t)nbk * 8, st), ticket(4, st);
     check_cuda(cudaMemsetAsync(ticket.p, 0, 4, st), "memset");
     const unsigned grid2 = (unsigned)std::max<uint32_t>(1, std::min<uint32_t>(nbk, (uint32_t)sms * 2));
     Scratch stacks((size_t)grid2 * kStackCap * sizeof(StackEnt), st);
     Scratch splscr((size_t)grid2 * (CAP / 2) * NW * 8, st);
     auto k2 = k_level2<Src, MODE>;
-    check_cuda(cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM), "attr");
+    smem_attr(k2, Cfg::SMEM);
     StageScope ss2(ST_LEVEL2, st);
     note_launch(ST_LEVEL2);
     note_launch(ST_LEVEL2);  // k_level2 and the scan below
@@ -1030,7 +1258,8 @@ static paulib_sum* product_mode(const paulib_sum* a, const paulib_sum* b, cudaSt
         ac = fa.as<V>();
         bc = fb.as<V>();
     }
-    Src src{a->keys, b->keys, a->pbase, b->pbase, ac, bc, (uint32_t)a->n_terms};
+    // the same sum on both sides: only i <= j pairs are generated
+    Src src{a->keys, b->keys, a->pbase, b->pbase, ac, bc, (uint32_t)a->n_terms, a == b ? 1u : 0u};
     return finish<Src, MODE>(src, R, (uint32_t)b->n_terms, a->n_qubits, st);
 }
 
@@ -1084,18 +1313,357 @@ paulib_sum* canon_terms(const paulib_sum* in, int mode, cudaStream_t st) {
     return nullptr;
 }
 
-void canon_batched(int32_t batch, const paulib_sum* const* a, const paulib_sum* const* b, int mode,
-                   cudaStream_t st, paulib_sum** out) {
-    int32_t done = 0;
-    try {
-        for (; done < batch; ++done) out[done] = canon_product(a[done], b[done], mode, st);
-    } catch (...) {
-        for (int32_t i = 0; i < done; ++i) {
-            sum_free(out[i], st);
-            out[i] = nullptr;
+// ---------------------------------------------------------------- batched products
+//
+// Many independent products canonicalised together.  Problem b's records are
+// the global record range [r0s[b], r0s[b+1]); its products' keys are prefixed
+// by two words (b, 0), so the pipeline's single sort keeps problems apart and
+// emits them in order.  The output of problem b is then copied into its own
+// sum (capacity |A_b||B_b|).
+
+struct ProbDesc {
+    const uint64_t* ak;
+    const uint64_t* bk;
+    const uint8_t* ap;
+    const uint8_t* bp;
+    const void* ac;
+    const void* bc;
+    uint32_t na, nb;
+    uint64_t pad;
+};
+static_assert(sizeof(ProbDesc) == 64, "descriptor is one 64-byte record");
+
+struct OutDesc {
+    uint64_t* keys;
+    double2* coef;
+    uint8_t* pbase;
+    uint64_t pad;
+};
+
+template <int WP_, int MODE>
+struct BatchSrc {
+    static constexpr int WP = WP_;
+    static constexpr int NW = 2 * WP + 2;
+    using V = typename ValT<MODE>::T;
+    const ProbDesc* probs;
+    const uint32_t* r0s;
+    uint32_t nprob;
+    // problem of record r: the largest b with r0s[b] <= r (empty problems are skipped)
+    __device__ __forceinline__ uint32_t find(uint32_t r) const {
+        uint32_t lo = 0, hi = nprob;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(r0s + mid) <= r) lo = mid; else hi = mid;
         }
+        return lo;
+    }
+    __device__ __forceinline__ uint32_t kp(uint32_t r, uint64_t (&k)[NW], bool want_phase) const {
+        const uint32_t b = find(r);
+        const ProbDesc d = probs[b];
+        const uint32_t q = r - __ldg(r0s + b);
+        const uint32_t j = q / d.na, i = q - j * d.na;
+        uint64_t a[2 * WP], bb[2 * WP], o[2 * WP];
+        key_load_g<2 * WP>(d.ak, i, a);
+        key_load_g<2 * WP>(d.bk, j, bb);
+        uint32_t ph = 0;
+        if (want_phase) {
+            ph = string_product<WP>(a, bb, __ldg(d.ap + i), __ldg(d.bp + j), o);
+        } else {
+#pragma unroll
+            for (int w = 0; w < 2 * WP; ++w) o[w] = a[w] ^ bb[w];
+        }
+        k[0] = b;
+        k[1] = 0;
+#pragma unroll
+        for (int w = 0; w < 2 * WP; ++w) k[2 + w] = o[w];
+        return ph;
+    }
+    __device__ __forceinline__ void key(uint32_t r, uint64_t (&k)[NW]) const { kp(r, k, false); }
+    __device__ __forceinline__ uint32_t keyphase(uint32_t r, uint64_t (&k)[NW]) const { return kp(r, k, true); }
+    __device__ __forceinline__ V coefv(uint32_t r, uint32_t ph) const {
+        const uint32_t b = find(r);
+        const ProbDesc d = probs[b];
+        const uint32_t q = r - __ldg(r0s + b);
+        const uint32_t j = q / d.na, i = q - j * d.na;
+        return rot_v(mul_v(static_cast<const V*>(d.ac)[i], static_cast<const V*>(d.bc)[j]), ph);
+    }
+    __device__ __forceinline__ V value(uint32_t r, uint64_t (&k)[NW]) const { return coefv(r, keyphase(r, k)); }
+};
+
+// Distinct output strings per problem.  Within a coarse range the merged
+// terms are in key order, so problems form runs; each thread adds its runs.
+template <int NW>
+__global__ void __launch_bounds__(256) k_batch_counts(uint32_t nbk, const uint64_t* __restrict__ boff,
+                                                      const uint64_t* __restrict__ uoff,
+                                                      const uint64_t* __restrict__ Tkeys,
+                                                      unsigned long long* counts) {
+    for (uint32_t c = blockIdx.x; c < nbk; c += gridDim.x) {
+        const uint64_t src0 = boff[c];
+        const uint64_t cnt = uoff[c + 1] - uoff[c];
+        const uint64_t per = (cnt + blockDim.x - 1) / blockDim.x;
+        const uint64_t t0 = (uint64_t)threadIdx.x * per;
+        const uint64_t t1 = mn<uint64_t>(cnt, t0 + per);
+        uint64_t run = 0, cur = ~0ull;
+        for (uint64_t t = t0; t < t1; ++t) {
+            const uint64_t b = Tkeys[(src0 + t) * NW];
+            if (b != cur) {
+                if (run) atomicAdd(&counts[cur], (unsigned long long)run);
+                cur = b;
+                run = 0;
+            }
+            ++run;
+        }
+        if (run) atomicAdd(&counts[cur], (unsigned long long)run);
+    }
+}
+
+template <int WP>
+__global__ void __launch_bounds__(256) k_batch_scatter(uint32_t nbk, const uint64_t* __restrict__ boff,
+                                                       const uint64_t* __restrict__ uoff,
+                                                       const uint64_t* __restrict__ Tkeys,
+                                                       const double2* __restrict__ Tcoef,
+                                                       const uint64_t* __restrict__ pstart,
+                                                       const OutDesc* __restrict__ outs) {
+    constexpr int NW = 2 * WP + 2;
+    for (uint32_t c = blockIdx.x; c < nbk; c += gridDim.x) {
+        const uint64_t src0 = boff[c];
+        const uint64_t dst0 = uoff[c];
+        const uint64_t cnt = uoff[c + 1] - dst0;
+        for (uint64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+            uint64_t k[NW];
+            key_load_g<NW>(Tkeys, src0 + t, k);
+            const uint32_t b = (uint32_t)k[0];
+            const uint64_t pos = dst0 + t - pstart[b];
+            const OutDesc o = outs[b];
+            uint64_t kk[2 * WP];
+#pragma unroll
+            for (int w = 0; w < 2 * WP; ++w) kk[w] = k[2 + w];
+            key_store<2 * WP>(o.keys, pos, kk);
+            o.coef[pos] = Tcoef[src0 + t];
+            o.pbase[pos] = (uint8_t)normal_phase<WP>(kk, 0u);
+        }
+    }
+}
+
+// FP32 copies of operand coefficients: job j converts n[j] values.
+struct F32Job {
+    const double2* src;
+    float2* dst;
+    uint64_t n;
+    uint64_t pad;
+};
+__global__ void k_batch_to_f32(const F32Job* jobs, uint32_t njobs) {
+    for (uint32_t j = blockIdx.x; j < njobs; j += gridDim.x) {
+        const F32Job jb = jobs[j];
+        for (uint64_t t = threadIdx.x; t < jb.n; t += blockDim.x)
+            jb.dst[t] = make_float2(__double2float_rn(jb.src[t].x), __double2float_rn(jb.src[t].y));
+    }
+}
+
+}  // namespace paulib
+
+struct paulib_batch_plan {
+    int32_t batch = 0, n_qubits = 0, WP = 0, mode = 0;
+    uint64_t R = 0;
+    std::vector<paulib_sum*> outs;
+    void* desc = nullptr;  // descriptors, offsets, counters (one allocation)
+    void* f32 = nullptr;   // FP32 coefficient copies (mixed-precision modes)
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    bool released = false;
+    paulib::ProbDesc* d_probs = nullptr;
+    uint32_t* d_r0s = nullptr;
+    paulib::OutDesc* d_outs = nullptr;
+    unsigned long long* d_counts = nullptr;
+    uint64_t* d_pstart = nullptr;
+    int32_t* d_err = nullptr;
+};
+
+namespace paulib {
+
+template <int WP, int MODE>
+static void batch_launch_impl(paulib_batch_plan* p, cudaStream_t st) {
+    using Src = BatchSrc<WP, MODE>;
+    constexpr int NW = Src::NW;
+    check_cuda(cudaMemsetAsync(p->d_counts, 0, (size_t)p->batch * 8, st), "memset counts");
+    check_cuda(cudaMemsetAsync(p->d_err, 0, 4, st), "memset err");
+    if (p->R == 0) return;
+    Src src{p->d_probs, p->d_r0s, (uint32_t)p->batch};
+    Staged sg;
+    run_pipeline<Src, MODE>(src, (uint32_t)p->R, 0, st, sg);
+    StageScope ss(ST_COMPACT, st);
+    const unsigned grid = std::max<uint32_t>(1, std::min<uint32_t>(sg.nbk, (uint32_t)device_sm_count() * 8));
+    k_or_err<<<1, 32, 0, st>>>(sg.err.as<int32_t>(), p->d_err);
+    k_batch_counts<NW><<<grid, 256, 0, st>>>(sg.nbk, sg.boff.as<uint64_t>(), sg.uoff.as<uint64_t>(),
+                                             sg.Tkeys.as<uint64_t>(), p->d_counts);
+    k_scan_u64<<<1, 1024, 0, st>>>(reinterpret_cast<const uint64_t*>(p->d_counts), (uint32_t)p->batch, p->d_pstart);
+    k_batch_scatter<WP><<<grid, 256, 0, st>>>(sg.nbk, sg.boff.as<uint64_t>(), sg.uoff.as<uint64_t>(),
+                                              sg.Tkeys.as<uint64_t>(), sg.Tcoef.as<double2>(), p->d_pstart,
+                                              p->d_outs);
+    for (int q = 0; q < 4; ++q) note_launch(ST_COMPACT);
+    check_cuda(cudaGetLastError(), "batched output");
+}
+
+static void batch_launch(paulib_batch_plan* p, cudaStream_t st) {
+#define L(WPv)                                                                                  \
+    {                                                                                           \
+        if (p->mode == M_FP64) batch_launch_impl<WPv, M_FP64>(p, st);                           \
+        else if (p->mode == M_F32_D64) batch_launch_impl<WPv, M_F32_D64>(p, st);                \
+        else batch_launch_impl<WPv, M_F32_TWOSUM>(p, st);                                       \
+    }
+    PAULIB_DISPATCH_WP(p->WP, L);
+#undef L
+}
+
+struct ArenaRecordGuard {
+    bool on = true;
+    ArenaRecordGuard() { arena_record_begin(); }
+    size_t end() { on = false; return arena_record_end(); }
+    ~ArenaRecordGuard() { if (on) arena_record_end(); }
+};
+struct ArenaReplayGuard {
+    ArenaReplayGuard(void* b, size_t n) { arena_replay_begin(b, n); }
+    ~ArenaReplayGuard() { arena_replay_end(); }
+};
+
+static void plan_free(paulib_batch_plan* p, cudaStream_t st) {
+    if (!p) return;
+    if (!p->released)
+        for (paulib_sum* s : p->outs) sum_free(s, st);
+    dev_free(p->desc, st);
+    dev_free(p->f32, st);
+    dev_free(p->arena, st);
+    delete p;
+}
+
+paulib_batch_plan* batch_plan_create(int32_t batch, const paulib_sum* const* a, const paulib_sum* const* b,
+                                     int mode, cudaStream_t st) {
+    paulib_batch_plan* p = new paulib_batch_plan;
+    try {
+        p->batch = batch;
+        p->n_qubits = a[0]->n_qubits;
+        p->WP = a[0]->WP;
+        p->mode = mode;
+        std::vector<uint32_t> r0s(batch + 1, 0);
+        uint64_t R = 0;
+        for (int32_t q = 0; q < batch; ++q) {
+            r0s[q] = (uint32_t)R;
+            R += (uint64_t)a[q]->n_terms * (uint64_t)b[q]->n_terms;
+            if (R >= ((uint64_t)1 << 32) - 1) fail(PAULIB_ERR_UNSUPPORTED, "batched products need sum |A_b||B_b| < 2^32");
+        }
+        r0s[batch] = (uint32_t)R;
+        p->R = R;
+        p->outs.assign(batch, nullptr);
+        for (int32_t q = 0; q < batch; ++q) {
+            p->outs[q] = sum_alloc(p->n_qubits, a[q]->n_terms * b[q]->n_terms, false, st);
+            p->outs[q]->is_canonical = 1;
+            p->outs[q]->plan_owned = true;
+            p->outs[q]->n_terms = 0;
+        }
+        // descriptor block
+        const size_t szP = (size_t)batch * sizeof(ProbDesc);
+        const size_t szR = ((size_t)(batch + 1) * 4 + 255) / 256 * 256;
+        const size_t szO = (size_t)batch * sizeof(OutDesc);
+        const size_t szC = ((size_t)batch * 8 + 255) / 256 * 256;
+        const size_t szS = ((size_t)(batch + 1) * 8 + 255) / 256 * 256;
+        const size_t total = szP + szR + szO + szC + szS + 256;
+        p->desc = dev_alloc(total, st);
+        char* base = static_cast<char*>(p->desc);
+        p->d_probs = reinterpret_cast<ProbDesc*>(base);
+        p->d_r0s = reinterpret_cast<uint32_t*>(base + szP);
+        p->d_outs = reinterpret_cast<OutDesc*>(base + szP + szR);
+        p->d_counts = reinterpret_cast<unsigned long long*>(base + szP + szR + szO);
+        p->d_pstart = reinterpret_cast<uint64_t*>(base + szP + szR + szO + szC);
+        p->d_err = reinterpret_cast<int32_t*>(base + szP + szR + szO + szC + szS);
+        std::vector<ProbDesc> hp(batch);
+        std::vector<OutDesc> ho(batch);
+        std::vector<F32Job> jobs;
+        size_t f32_total = 0;
+        if (mode != M_FP64)
+            for (int32_t q = 0; q < batch; ++q) f32_total += (size_t)(a[q]->n_terms + b[q]->n_terms);
+        if (f32_total) p->f32 = dev_alloc(f32_total * sizeof(float2), st);
+        float2* f = static_cast<float2*>(p->f32);
+        for (int32_t q = 0; q < batch; ++q) {
+            ProbDesc& d = hp[q];
+            d.ak = a[q]->keys;
+            d.bk = b[q]->keys;
+            d.ap = a[q]->pbase;
+            d.bp = b[q]->pbase;
+            d.na = (uint32_t)a[q]->n_terms;
+            d.nb = (uint32_t)b[q]->n_terms;
+            d.pad = 0;
+            if (mode == M_FP64) {
+                d.ac = a[q]->coef;
+                d.bc = b[q]->coef;
+            } else {
+                d.ac = f;
+                if (a[q]->n_terms) jobs.push_back(F32Job{a[q]->coef, f, (uint64_t)a[q]->n_terms, 0});
+                f += a[q]->n_terms;
+                d.bc = f;
+                if (b[q]->n_terms) jobs.push_back(F32Job{b[q]->coef, f, (uint64_t)b[q]->n_terms, 0});
+                f += b[q]->n_terms;
+            }
+            ho[q] = OutDesc{p->outs[q]->keys, p->outs[q]->coef, p->outs[q]->pbase, 0};
+        }
+        check_cuda(cudaMemcpyAsync(p->d_probs, hp.data(), szP, cudaMemcpyHostToDevice, st), "desc copy");
+        check_cuda(cudaMemcpyAsync(p->d_r0s, r0s.data(), (size_t)(batch + 1) * 4, cudaMemcpyHostToDevice, st), "r0 copy");
+        check_cuda(cudaMemcpyAsync(p->d_outs, ho.data(), szO, cudaMemcpyHostToDevice, st), "out copy");
+        Scratch jobs_d;
+        if (!jobs.empty()) {
+            jobs_d = Scratch(jobs.size() * sizeof(F32Job), st);
+            check_cuda(cudaMemcpyAsync(jobs_d.p, jobs.data(), jobs.size() * sizeof(F32Job), cudaMemcpyHostToDevice, st),
+                       "job copy");
+            k_batch_to_f32<<<std::min<size_t>(jobs.size(), 4096), 256, 0, st>>>(jobs_d.as<F32Job>(), (uint32_t)jobs.size());
+            note_launch(ST_CONVERT);
+            check_cuda(cudaGetLastError(), "k_batch_to_f32");
+        }
+        // one full run that records the workspace it asks for
+        {
+            ArenaRecordGuard rec;
+            batch_launch(p, st);
+            p->arena_bytes = rec.end();
+        }
+        if (p->arena_bytes) p->arena = dev_alloc(p->arena_bytes, st);
+        check_cuda(cudaStreamSynchronize(st), "plan sync");  // host vectors above must outlive their copies
+    } catch (...) {
+        plan_free(p, st);
         throw;
     }
+    return p;
+}
+
+void batch_plan_launch(paulib_batch_plan* p, cudaStream_t st) {
+    ArenaReplayGuard g(p->arena, p->arena_bytes);
+    batch_launch(p, st);
+}
+
+void batch_plan_outputs(paulib_batch_plan* p, cudaStream_t st, paulib_sum** out) {
+    std::vector<unsigned long long> cnt(p->batch);
+    int32_t e = 0;
+    check_cuda(cudaMemcpyAsync(cnt.data(), p->d_counts, (size_t)p->batch * 8, cudaMemcpyDeviceToHost, st), "count copy");
+    check_cuda(cudaMemcpyAsync(&e, p->d_err, 4, cudaMemcpyDeviceToHost, st), "err copy");
+    check_cuda(cudaStreamSynchronize(st), "outputs sync");
+    if (e) fail(PAULIB_ERR_INTERNAL, "batched canonicalisation failed on device (error word " + std::to_string(e) + ")");
+    for (int32_t q = 0; q < p->batch; ++q) {
+        p->outs[q]->n_terms = (int64_t)cnt[q];
+        out[q] = p->outs[q];
+    }
+}
+
+void batch_plan_destroy(paulib_batch_plan* p) { plan_free(p, nullptr); }
+
+void canon_batched(int32_t batch, const paulib_sum* const* a, const paulib_sum* const* b, int mode,
+                   cudaStream_t st, paulib_sum** out) {
+    paulib_batch_plan* p = batch_plan_create(batch, a, b, mode, st);
+    try {
+        batch_plan_outputs(p, st, out);
+    } catch (...) {
+        plan_free(p, st);
+        throw;
+    }
+    for (paulib_sum* s : p->outs) s->plan_owned = false;  // ownership passes to the caller
+    p->released = true;
+    plan_free(p, st);
 }
 
 // ---------------------------------------------------------------- allocation-free product

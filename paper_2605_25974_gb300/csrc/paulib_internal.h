@@ -20,6 +20,7 @@ struct paulib_sum {
     uint8_t* phase = nullptr;   // [n_terms] own phase exponent, or null when all zero
     void* block = nullptr;      // the single allocation
     size_t block_bytes = 0;
+    bool plan_owned = false;    // storage of a batched plan's output: destroy is a no-op
 };
 
 namespace paulib {
@@ -34,6 +35,19 @@ void check_cuda(cudaError_t e, const char* what);
 
 void* dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void* p, cudaStream_t s);
+
+// Workspace arena for prepared (plan) launches.  While recording, every
+// dev_alloc is served normally and its size is added up; while replaying,
+// dev_alloc hands out consecutive pieces of one pre-allocated block and
+// dev_free does nothing, so a launch neither allocates nor frees.  The
+// pipeline's allocation sequence depends only on operand sizes, so a replay
+// asks for exactly the recorded pieces.  Replay also marks the thread
+// capture-safe: no host synchronisation, no event timing, no attribute calls.
+void arena_record_begin();
+size_t arena_record_end();
+void arena_replay_begin(void* base, size_t bytes);
+void arena_replay_end();
+bool capture_safe();
 
 // A scratch buffer freed (stream ordered) when it goes out of scope.
 struct Scratch {
@@ -104,6 +118,12 @@ paulib_sum* canon_product(const paulib_sum* a, const paulib_sum* b, int mode, cu
 paulib_sum* canon_terms(const paulib_sum* in, int mode, cudaStream_t st);
 void canon_batched(int32_t batch, const paulib_sum* const* a, const paulib_sum* const* b, int mode,
                    cudaStream_t st, paulib_sum** out);
+
+paulib_batch_plan* batch_plan_create(int32_t batch, const paulib_sum* const* a, const paulib_sum* const* b,
+                                     int mode, cudaStream_t st);
+void batch_plan_launch(paulib_batch_plan* p, cudaStream_t st);
+void batch_plan_outputs(paulib_batch_plan* p, cudaStream_t st, paulib_sum** out);
+void batch_plan_destroy(paulib_batch_plan* p);
 
 // Allocation-free canonical product using the library's static scratch
 // array (see paulib_multiply_noalloc in include/paulib.h).

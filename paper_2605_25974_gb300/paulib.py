@@ -25,7 +25,8 @@ OUT_RAW, OUT_CANONICAL = 0, 1
 EXPORTED = ["paulib_abi_version", "paulib_sum_create", "paulib_sum_info", "paulib_sum_export",
             "paulib_sum_destroy", "paulib_multiply", "paulib_compress", "paulib_multiply_batched",
             "paulib_last_error", "paulib_set_allocator", "paulib_timing_enable", "paulib_timing_read",
-            "paulib_multiply_noalloc"]
+            "paulib_multiply_noalloc", "paulib_batch_plan_create", "paulib_batch_plan_launch",
+            "paulib_batch_plan_outputs", "paulib_batch_plan_destroy"]
 STAGES = ["convert", "sample", "count", "scatter", "level2", "compact", "raw", "export"]
 
 
@@ -66,6 +67,15 @@ def load(path: Optional[str] = None):
     lib.paulib_multiply_batched.argtypes = [_i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32, _vp,
                                             ctypes.POINTER(_vp)]
     lib.paulib_last_error.restype = ctypes.c_char_p
+    lib.paulib_batch_plan_create.argtypes = [_i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32, _vp,
+                                             ctypes.POINTER(_vp)]
+    lib.paulib_batch_plan_create.restype = _i32
+    lib.paulib_batch_plan_launch.argtypes = [_vp, _vp]
+    lib.paulib_batch_plan_launch.restype = _i32
+    lib.paulib_batch_plan_outputs.argtypes = [_vp, _vp, ctypes.POINTER(_vp)]
+    lib.paulib_batch_plan_outputs.restype = _i32
+    lib.paulib_batch_plan_destroy.argtypes = [_vp]
+    lib.paulib_batch_plan_destroy.restype = None
     lib.paulib_timing_enable.argtypes = [_i32]
     lib.paulib_timing_enable.restype = _i32
     lib.paulib_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
@@ -207,6 +217,48 @@ def multiply_batched(a: Sequence[PauliSum], b: Sequence[PauliSum], precision="fp
     O = (_vp * n)()
     _check(load().paulib_multiply_batched(n, A, B, _prec(precision), _vp(_stream(stream)), O))
     return [PauliSum(O[i]) for i in range(n)]
+
+
+class _Borrowed(PauliSum):
+    """A sum owned by a batch plan: never destroyed through this handle."""
+
+    def close(self):
+        self._h = 0
+
+
+class BatchPlan:
+    """Prepared batched product: ``launch`` enqueues it without allocating or
+    synchronising (capturable in a CUDA graph); ``outputs`` syncs and returns
+    the plan-owned canonical sums of the last launch."""
+
+    def __init__(self, a: Sequence[PauliSum], b: Sequence[PauliSum], precision="fp64", stream=None):
+        n = len(a)
+        self.batch = n
+        self._keep = (list(a), list(b))
+        A = (_vp * n)(*[s.handle for s in a])
+        B = (_vp * n)(*[s.handle for s in b])
+        out = _vp()
+        _check(load().paulib_batch_plan_create(n, A, B, _prec(precision), _vp(_stream(stream)), ctypes.byref(out)))
+        self._h = out.value
+
+    def launch(self, stream=None):
+        _check(load().paulib_batch_plan_launch(_vp(self._h), _vp(_stream(stream))))
+
+    def outputs(self, stream=None) -> List[PauliSum]:
+        O = (_vp * self.batch)()
+        _check(load().paulib_batch_plan_outputs(_vp(self._h), _vp(_stream(stream)), O))
+        return [_Borrowed(O[i]) for i in range(self.batch)]
+
+    def close(self):
+        if self._h:
+            load().paulib_batch_plan_destroy(_vp(self._h))
+            self._h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def timing_enable(on: bool = True):

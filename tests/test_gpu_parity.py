@@ -91,6 +91,32 @@ def test_jw_hh_scaled(lib, oracle, n, m):
     assert ocnt.max() == m  # identity term
 
 
+@pytest.mark.parametrize("n,m", [(100, 700), (200, 400), (20, 900), (30, 60)])
+def test_same_operand_symmetric_path(lib, oracle, n, m):
+    # multiply(H, H) with one handle: only pairs i <= j are generated, each
+    # off-diagonal pair counted twice or cancelled by its commutation sign.
+    from paper_2605_25974_gb300 import workloads as wl
+    h = wl.jw(n=n, m=m, seed=2000 + n)
+    ox, oz, oc, oabs, _ = oracle.multiply_canonical(n, h.as_tuple(), h.as_tuple())
+    for prec, tol in (("fp64", TOL64), ("fp32_fp64merge", fp32_tolerance())):
+        with gpu_sum(lib, h) as g, lib.multiply(g, g, prec) as gc:
+            x, z, c, _ = gc.export()
+        check_canonical(x, z, c, ox, oz, oc, oabs, tol=tol)
+
+
+def test_same_operand_with_repeats_and_phases(lib, oracle):
+    from paper_2605_25974_gb300 import workloads as wl
+    rng = wl.rng_for(31)
+    n = 70
+    ux, uz = wl.weighted_random(rng, n, 300, 1, 10)
+    idx = rng.integers(0, 300, 2500)
+    s = wl.SumArrays(n, ux[:, idx].copy(), uz[:, idx].copy(), wl.coeffs_normal(rng, 2500),
+                     rng.integers(0, 4, 2500).astype(np.uint8))
+    with gpu_sum(lib, s) as g, lib.multiply(g, g) as gc:
+        x, z, c, _ = gc.export()
+    check_canonical(x, z, c, *oracle.multiply_canonical(n, s.as_tuple(), s.as_tuple())[:4])
+
+
 @pytest.mark.parametrize("n,ma,mb", [(500, 3000, 7), (500, 16, 8), (130, 1000, 33), (1024, 300, 5),
                                      (65, 2500, 3)])
 def test_random_weighted_products(lib, oracle, n, ma, mb):
@@ -240,5 +266,56 @@ def test_batched_matches_per_problem_oracle(lib, oracle):
     for (a, b), o in zip(probs, outs):
         x, z, c, _ = o.export()
         check_canonical(x, z, c, *oracle.multiply_canonical(a.n, a.as_tuple(), b.as_tuple())[:4])
+    for s in As + Bs + outs:
+        s.close()
+
+
+def test_batch_plan_relaunch_and_graph_replay(lib, oracle):
+    # A prepared plan relaunched (and replayed from a captured CUDA graph)
+    # gives the same canonical outputs as the oracle, problem by problem.
+    import torch
+    from paper_2605_25974_gb300 import workloads as wl
+    probs = wl.batch(problems=9, amax=2000)
+    probs.append((probs[0][0], wl.SumArrays(500, probs[0][1].x[:, :0].copy(), probs[0][1].z[:, :0].copy(),
+                                            probs[0][1].c[:0].copy())))  # an empty problem
+    As = [gpu_sum(lib, a) for a, _ in probs]
+    Bs = [gpu_sum(lib, b) for _, b in probs]
+    expect = [oracle.multiply_canonical(a.n, a.as_tuple(), b.as_tuple()) for a, b in probs]
+
+    def check(outs):
+        for (ox, oz, oc, oabs, _), o in zip(expect, outs):
+            x, z, c, _ = o.export()
+            check_canonical(x, z, c, ox, oz, oc, oabs)
+
+    plan = lib.BatchPlan(As, Bs, "fp64")
+    check(plan.outputs())              # the run made while preparing
+    plan.launch()
+    check(plan.outputs())              # a plain relaunch
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.launch(stream=s)
+    for _ in range(2):
+        g.replay()
+        torch.cuda.current_stream().wait_stream(s)
+        check(plan.outputs())
+    plan.close()
+    for t in As + Bs:
+        t.close()
+
+
+@pytest.mark.parametrize("mode", ["fp32_fp64merge", "fp32_twosum"])
+def test_batched_mixed_precision(lib, oracle, mode):
+    from paper_2605_25974_gb300 import workloads as wl
+    probs = wl.batch(problems=6, amax=1500)
+    As = [gpu_sum(lib, a) for a, _ in probs]
+    Bs = [gpu_sum(lib, b) for _, b in probs]
+    outs = lib.multiply_batched(As, Bs, mode)
+    for (a, b), o in zip(probs, outs):
+        x, z, c, _ = o.export()
+        check_canonical(x, z, c, *oracle.multiply_canonical(a.n, a.as_tuple(), b.as_tuple())[:4],
+                        tol=fp32_tolerance())
     for s in As + Bs + outs:
         s.close()
