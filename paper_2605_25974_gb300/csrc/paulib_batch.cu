@@ -1,0 +1,360 @@
+// paulib_batch.cu -- batched canonical products and the prepared, graph-
+// capturable batch plan; the pipeline is in paulib_pipeline.cuh.
+#include "paulib_pipeline.cuh"
+
+namespace paulib {
+
+// ---------------------------------------------------------------- batched products
+//
+// Many independent products canonicalised together.  Problem b's records are
+// the global record range [r0s[b], r0s[b+1]); its products' keys are prefixed
+// by two words (b, 0), so the pipeline's single sort keeps problems apart and
+// emits them in order.  The output of problem b is then copied into its own
+// sum (capacity |A_b||B_b|).
+
+struct ProbDesc {
+    const uint64_t* ak;
+    const uint64_t* bk;
+    const uint8_t* ap;
+    const uint8_t* bp;
+    const void* ac;
+    const void* bc;
+    uint32_t na, nb;
+    uint64_t pad;
+};
+static_assert(sizeof(ProbDesc) == 64, "descriptor is one 64-byte record");
+
+struct OutDesc {
+    uint64_t* keys;
+    double2* coef;
+    uint8_t* pbase;
+    uint64_t pad;
+};
+
+template <int WP_, int MODE>
+struct BatchSrc {
+    static constexpr int WP = WP_;
+    static constexpr int NW = 2 * WP + 2;
+    using V = typename ValT<MODE>::T;
+    const ProbDesc* probs;
+    const uint32_t* r0s;
+    uint32_t nprob;
+    // problem of record r: the largest b with r0s[b] <= r (empty problems are skipped)
+    __device__ __forceinline__ uint32_t find(uint32_t r) const {
+        uint32_t lo = 0, hi = nprob;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(r0s + mid) <= r) lo = mid; else hi = mid;
+        }
+        return lo;
+    }
+    __device__ __forceinline__ uint32_t kp(uint32_t r, uint64_t (&k)[NW], bool want_phase) const {
+        const uint32_t b = find(r);
+        const ProbDesc d = probs[b];
+        const uint32_t q = r - __ldg(r0s + b);
+        const uint32_t j = q / d.na, i = q - j * d.na;
+        uint64_t a[2 * WP], bb[2 * WP], o[2 * WP];
+        key_load_g<2 * WP>(d.ak, i, a);
+        key_load_g<2 * WP>(d.bk, j, bb);
+        uint32_t ph = 0;
+        if (want_phase) {
+            ph = string_product<WP>(a, bb, __ldg(d.ap + i), __ldg(d.bp + j), o);
+        } else {
+#pragma unroll
+            for (int w = 0; w < 2 * WP; ++w) o[w] = a[w] ^ bb[w];
+        }
+        k[0] = b;
+        k[1] = 0;
+#pragma unroll
+        for (int w = 0; w < 2 * WP; ++w) k[2 + w] = o[w];
+        return ph;
+    }
+    __device__ __forceinline__ void key(uint32_t r, uint64_t (&k)[NW]) const { kp(r, k, false); }
+    __device__ __forceinline__ uint32_t keyphase(uint32_t r, uint64_t (&k)[NW]) const { return kp(r, k, true); }
+    __device__ __forceinline__ V coefv(uint32_t r, uint32_t ph) const {
+        const uint32_t b = find(r);
+        const ProbDesc d = probs[b];
+        const uint32_t q = r - __ldg(r0s + b);
+        const uint32_t j = q / d.na, i = q - j * d.na;
+        return rot_v(mul_v(static_cast<const V*>(d.ac)[i], static_cast<const V*>(d.bc)[j]), ph);
+    }
+    __device__ __forceinline__ V value(uint32_t r, uint64_t (&k)[NW]) const { return coefv(r, keyphase(r, k)); }
+};
+
+// Distinct output strings per problem.  Within a coarse range the merged
+// terms are in key order, so problems form runs; each thread adds its runs.
+template <int NW>
+__global__ void __launch_bounds__(256) k_batch_counts(uint32_t nbk, const uint64_t* __restrict__ boff,
+                                                      const uint64_t* __restrict__ uoff,
+                                                      const uint64_t* __restrict__ Tkeys,
+                                                      unsigned long long* counts) {
+    for (uint32_t c = blockIdx.x; c < nbk; c += gridDim.x) {
+        const uint64_t src0 = boff[c];
+        const uint64_t cnt = uoff[c + 1] - uoff[c];
+        const uint64_t per = (cnt + blockDim.x - 1) / blockDim.x;
+        const uint64_t t0 = (uint64_t)threadIdx.x * per;
+        const uint64_t t1 = mn<uint64_t>(cnt, t0 + per);
+        uint64_t run = 0, cur = ~0ull;
+        for (uint64_t t = t0; t < t1; ++t) {
+            const uint64_t b = Tkeys[(src0 + t) * NW];
+            if (b != cur) {
+                if (run) atomicAdd(&counts[cur], (unsigned long long)run);
+                cur = b;
+                run = 0;
+            }
+            ++run;
+        }
+        if (run) atomicAdd(&counts[cur], (unsigned long long)run);
+    }
+}
+
+template <int WP>
+__global__ void __launch_bounds__(256) k_batch_scatter(uint32_t nbk, const uint64_t* __restrict__ boff,
+                                                       const uint64_t* __restrict__ uoff,
+                                                       const uint64_t* __restrict__ Tkeys,
+                                                       const double2* __restrict__ Tcoef,
+                                                       const uint64_t* __restrict__ pstart,
+                                                       const OutDesc* __restrict__ outs) {
+    constexpr int NW = 2 * WP + 2;
+    for (uint32_t c = blockIdx.x; c < nbk; c += gridDim.x) {
+        const uint64_t src0 = boff[c];
+        const uint64_t dst0 = uoff[c];
+        const uint64_t cnt = uoff[c + 1] - dst0;
+        for (uint64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+            uint64_t k[NW];
+            key_load_g<NW>(Tkeys, src0 + t, k);
+            const uint32_t b = (uint32_t)k[0];
+            const uint64_t pos = dst0 + t - pstart[b];
+            const OutDesc o = outs[b];
+            uint64_t kk[2 * WP];
+#pragma unroll
+            for (int w = 0; w < 2 * WP; ++w) kk[w] = k[2 + w];
+            key_store<2 * WP>(o.keys, pos, kk);
+            o.coef[pos] = Tcoef[src0 + t];
+            o.pbase[pos] = (uint8_t)normal_phase<WP>(kk, 0u);
+        }
+    }
+}
+
+// FP32 copies of operand coefficients: job j converts n[j] values.
+struct F32Job {
+    const double2* src;
+    float2* dst;
+    uint64_t n;
+    uint64_t pad;
+};
+__global__ void k_batch_to_f32(const F32Job* jobs, uint32_t njobs) {
+    for (uint32_t j = blockIdx.x; j < njobs; j += gridDim.x) {
+        const F32Job jb = jobs[j];
+        for (uint64_t t = threadIdx.x; t < jb.n; t += blockDim.x)
+            jb.dst[t] = make_float2(__double2float_rn(jb.src[t].x), __double2float_rn(jb.src[t].y));
+    }
+}
+
+}  // namespace paulib
+
+struct paulib_batch_plan {
+    int32_t batch = 0, n_qubits = 0, WP = 0, mode = 0;
+    uint64_t R = 0;
+    std::vector<paulib_sum*> outs;
+    void* desc = nullptr;  // descriptors, offsets, counters (one allocation)
+    void* f32 = nullptr;   // FP32 coefficient copies (mixed-precision modes)
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    bool released = false;
+    paulib::ProbDesc* d_probs = nullptr;
+    uint32_t* d_r0s = nullptr;
+    paulib::OutDesc* d_outs = nullptr;
+    unsigned long long* d_counts = nullptr;
+    uint64_t* d_pstart = nullptr;
+    int32_t* d_err = nullptr;
+};
+
+namespace paulib {
+
+template <int WP, int MODE>
+static void batch_launch_impl(paulib_batch_plan* p, cudaStream_t st) {
+    using Src = BatchSrc<WP, MODE>;
+    constexpr int NW = Src::NW;
+    check_cuda(cudaMemsetAsync(p->d_counts, 0, (size_t)p->batch * 8, st), "memset counts");
+    check_cuda(cudaMemsetAsync(p->d_err, 0, 4, st), "memset err");
+    if (p->R == 0) return;
+    Src src{p->d_probs, p->d_r0s, (uint32_t)p->batch};
+    Staged sg;
+    run_pipeline<Src, MODE>(src, (uint32_t)p->R, 0, st, sg);
+    StageScope ss(ST_COMPACT, st);
+    const unsigned grid = std::max<uint32_t>(1, std::min<uint32_t>(sg.nbk, (uint32_t)device_sm_count() * 8));
+    k_or_err<<<1, 32, 0, st>>>(sg.err.as<int32_t>(), p->d_err);
+    k_batch_counts<NW><<<grid, 256, 0, st>>>(sg.nbk, sg.boff.as<uint64_t>(), sg.uoff.as<uint64_t>(),
+                                             sg.Tkeys.as<uint64_t>(), p->d_counts);
+    k_scan_u64<<<1, 1024, 0, st>>>(reinterpret_cast<const uint64_t*>(p->d_counts), (uint32_t)p->batch, p->d_pstart);
+    k_batch_scatter<WP><<<grid, 256, 0, st>>>(sg.nbk, sg.boff.as<uint64_t>(), sg.uoff.as<uint64_t>(),
+                                              sg.Tkeys.as<uint64_t>(), sg.Tcoef.as<double2>(), p->d_pstart,
+                                              p->d_outs);
+    for (int q = 0; q < 4; ++q) note_launch(ST_COMPACT);
+    check_cuda(cudaGetLastError(), "batched output");
+}
+
+static void batch_launch(paulib_batch_plan* p, cudaStream_t st) {
+#define L(WPv)                                                                                  \
+    {                                                                                           \
+        if (p->mode == M_FP64) batch_launch_impl<WPv, M_FP64>(p, st);                           \
+        else if (p->mode == M_F32_D64) batch_launch_impl<WPv, M_F32_D64>(p, st);                \
+        else batch_launch_impl<WPv, M_F32_TWOSUM>(p, st);                                       \
+    }
+    PAULIB_DISPATCH_WP(p->WP, L);
+#undef L
+}
+
+struct ArenaRecordGuard {
+    bool on = true;
+    ArenaRecordGuard() { arena_record_begin(); }
+    size_t end() { on = false; return arena_record_end(); }
+    ~ArenaRecordGuard() { if (on) arena_record_end(); }
+};
+struct ArenaReplayGuard {
+    ArenaReplayGuard(void* b, size_t n) { arena_replay_begin(b, n); }
+    ~ArenaReplayGuard() { arena_replay_end(); }
+};
+
+static void plan_free(paulib_batch_plan* p, cudaStream_t st) {
+    if (!p) return;
+    if (!p->released)
+        for (paulib_sum* s : p->outs) sum_free(s, st);
+    dev_free(p->desc, st);
+    dev_free(p->f32, st);
+    dev_free(p->arena, st);
+    delete p;
+}
+
+paulib_batch_plan* batch_plan_create(int32_t batch, const paulib_sum* const* a, const paulib_sum* const* b,
+                                     int mode, cudaStream_t st) {
+    paulib_batch_plan* p = new paulib_batch_plan;
+    try {
+        p->batch = batch;
+        p->n_qubits = a[0]->n_qubits;
+        p->WP = a[0]->WP;
+        p->mode = mode;
+        std::vector<uint32_t> r0s(batch + 1, 0);
+        uint64_t R = 0;
+        for (int32_t q = 0; q < batch; ++q) {
+            r0s[q] = (uint32_t)R;
+            R += (uint64_t)a[q]->n_terms * (uint64_t)b[q]->n_terms;
+            if (R >= ((uint64_t)1 << 32) - 1) fail(PAULIB_ERR_UNSUPPORTED, "batched products need sum |A_b||B_b| < 2^32");
+        }
+        r0s[batch] = (uint32_t)R;
+        p->R = R;
+        p->outs.assign(batch, nullptr);
+        for (int32_t q = 0; q < batch; ++q) {
+            p->outs[q] = sum_alloc(p->n_qubits, a[q]->n_terms * b[q]->n_terms, false, st);
+            p->outs[q]->is_canonical = 1;
+            p->outs[q]->plan_owned = true;
+            p->outs[q]->n_terms = 0;
+        }
+        // descriptor block
+        const size_t szP = (size_t)batch * sizeof(ProbDesc);
+        const size_t szR = ((size_t)(batch + 1) * 4 + 255) / 256 * 256;
+        const size_t szO = (size_t)batch * sizeof(OutDesc);
+        const size_t szC = ((size_t)batch * 8 + 255) / 256 * 256;
+        const size_t szS = ((size_t)(batch + 1) * 8 + 255) / 256 * 256;
+        const size_t total = szP + szR + szO + szC + szS + 256;
+        p->desc = dev_alloc(total, st);
+        char* base = static_cast<char*>(p->desc);
+        p->d_probs = reinterpret_cast<ProbDesc*>(base);
+        p->d_r0s = reinterpret_cast<uint32_t*>(base + szP);
+        p->d_outs = reinterpret_cast<OutDesc*>(base + szP + szR);
+        p->d_counts = reinterpret_cast<unsigned long long*>(base + szP + szR + szO);
+        p->d_pstart = reinterpret_cast<uint64_t*>(base + szP + szR + szO + szC);
+        p->d_err = reinterpret_cast<int32_t*>(base + szP + szR + szO + szC + szS);
+        std::vector<ProbDesc> hp(batch);
+        std::vector<OutDesc> ho(batch);
+        std::vector<F32Job> jobs;
+        size_t f32_total = 0;
+        if (mode != M_FP64)
+            for (int32_t q = 0; q < batch; ++q) f32_total += (size_t)(a[q]->n_terms + b[q]->n_terms);
+        if (f32_total) p->f32 = dev_alloc(f32_total * sizeof(float2), st);
+        float2* f = static_cast<float2*>(p->f32);
+        for (int32_t q = 0; q < batch; ++q) {
+            ProbDesc& d = hp[q];
+            d.ak = a[q]->keys;
+            d.bk = b[q]->keys;
+            d.ap = a[q]->pbase;
+            d.bp = b[q]->pbase;
+            d.na = (uint32_t)a[q]->n_terms;
+            d.nb = (uint32_t)b[q]->n_terms;
+            d.pad = 0;
+            if (mode == M_FP64) {
+                d.ac = a[q]->coef;
+                d.bc = b[q]->coef;
+            } else {
+                d.ac = f;
+                if (a[q]->n_terms) jobs.push_back(F32Job{a[q]->coef, f, (uint64_t)a[q]->n_terms, 0});
+                f += a[q]->n_terms;
+                d.bc = f;
+                if (b[q]->n_terms) jobs.push_back(F32Job{b[q]->coef, f, (uint64_t)b[q]->n_terms, 0});
+                f += b[q]->n_terms;
+            }
+            ho[q] = OutDesc{p->outs[q]->keys, p->outs[q]->coef, p->outs[q]->pbase, 0};
+        }
+        check_cuda(cudaMemcpyAsync(p->d_probs, hp.data(), szP, cudaMemcpyHostToDevice, st), "desc copy");
+        check_cuda(cudaMemcpyAsync(p->d_r0s, r0s.data(), (size_t)(batch + 1) * 4, cudaMemcpyHostToDevice, st), "r0 copy");
+        check_cuda(cudaMemcpyAsync(p->d_outs, ho.data(), szO, cudaMemcpyHostToDevice, st), "out copy");
+        Scratch jobs_d;
+        if (!jobs.empty()) {
+            jobs_d = Scratch(jobs.size() * sizeof(F32Job), st);
+            check_cuda(cudaMemcpyAsync(jobs_d.p, jobs.data(), jobs.size() * sizeof(F32Job), cudaMemcpyHostToDevice, st),
+                       "job copy");
+            k_batch_to_f32<<<std::min<size_t>(jobs.size(), 4096), 256, 0, st>>>(jobs_d.as<F32Job>(), (uint32_t)jobs.size());
+            note_launch(ST_CONVERT);
+            check_cuda(cudaGetLastError(), "k_batch_to_f32");
+        }
+        // one full run that records the workspace it asks for
+        {
+            ArenaRecordGuard rec;
+            batch_launch(p, st);
+            p->arena_bytes = rec.end();
+        }
+        if (p->arena_bytes) p->arena = dev_alloc(p->arena_bytes, st);
+        check_cuda(cudaStreamSynchronize(st), "plan sync");  // host vectors above must outlive their copies
+    } catch (...) {
+        plan_free(p, st);
+        throw;
+    }
+    return p;
+}
+
+void batch_plan_launch(paulib_batch_plan* p, cudaStream_t st) {
+    ArenaReplayGuard g(p->arena, p->arena_bytes);
+    batch_launch(p, st);
+}
+
+void batch_plan_outputs(paulib_batch_plan* p, cudaStream_t st, paulib_sum** out) {
+    std::vector<unsigned long long> cnt(p->batch);
+    int32_t e = 0;
+    check_cuda(cudaMemcpyAsync(cnt.data(), p->d_counts, (size_t)p->batch * 8, cudaMemcpyDeviceToHost, st), "count copy");
+    check_cuda(cudaMemcpyAsync(&e, p->d_err, 4, cudaMemcpyDeviceToHost, st), "err copy");
+    check_cuda(cudaStreamSynchronize(st), "outputs sync");
+    if (e) fail(PAULIB_ERR_INTERNAL, "batched canonicalisation failed on device (error word " + std::to_string(e) + ")");
+    for (int32_t q = 0; q < p->batch; ++q) {
+        p->outs[q]->n_terms = (int64_t)cnt[q];
+        out[q] = p->outs[q];
+    }
+}
+
+void batch_plan_destroy(paulib_batch_plan* p) { plan_free(p, nullptr); }
+
+void canon_batched(int32_t batch, const paulib_sum* const* a, const paulib_sum* const* b, int mode,
+                   cudaStream_t st, paulib_sum** out) {
+    paulib_batch_plan* p = batch_plan_create(batch, a, b, mode, st);
+    try {
+        batch_plan_outputs(p, st, out);
+    } catch (...) {
+        plan_free(p, st);
+        throw;
+    }
+    for (paulib_sum* s : p->outs) s->plan_owned = false;  // ownership passes to the caller
+    p->released = true;
+    plan_free(p, st);
+}
+
+}  // namespace paulib

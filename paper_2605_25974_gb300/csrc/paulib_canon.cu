@@ -1,1287 +1,9 @@
-// paulib_canon.cu -- canonical form of a Pauli-sum product (PauLIB Sec. III-G
-// sort_and_combine, applied to the outer product of Sec. IV-C / V-C).
-//
-// The paper sorts an index array by the lexicographic key of the packed words
-// and then merges equal neighbours in one linear scan.  This file computes the
-// same result with a sample sort laid out for the GPU:
-//
-//   records   A record is a 32-bit index: a product (i, j) is r = j*|A| + i
-//             (Sec. IV-C's raw index); a term of a sum is its position.  Keys
-//             are never stored per product; they are recomputed from (i, j).
-//   level 1   Sample records, sort the sample (recursively, with this same
-//             pipeline), pick splitters, then count and scatter every record
-//             into its coarse key range.  For products the counting kernel
-//             walks the product space in tiles: left terms in registers, right
-//             terms in shared memory read as warp broadcasts.
-//   level 2   One CTA per coarse range keeps a worklist: a range larger than
-//             the shared-memory leaf capacity is split again by splitters taken
-//             from a sample of its own records; a leaf is gathered into shared
-//             memory, sorted by (key, record) with a bitonic network, and its
-//             equal-key runs are summed (Sec. III-G's merge).  A range whose
-//             keys are all equal (one heavily repeated string) is reduced
-//             without sorting.  Each coarse range writes its merged terms
-//             densely to a staging buffer.
-//   compact   Exclusive scan of the per-range term counts, then a copy into
-//             the output sum.
-//
-// Every device loop is bounded; failures raise a device error word that the
-// host turns into a status.
-#include <algorithm>
-#include <mutex>
-#include <vector>
-#include "paulib_device.cuh"
-#include "paulib_internal.h"
+// paulib_canon.cu -- canonical product of two sums (paulib_multiply with
+// PAULIB_OUT_CANONICAL) and the allocation-free variant; the pipeline itself
+// is in paulib_pipeline.cuh.
+#include "paulib_pipeline.cuh"
 
 namespace paulib {
-
-enum : int { M_FP64 = 0, M_F32_D64 = 1, M_F32_TWOSUM = 2 };
-enum : int32_t { ERR_NONE = 0, ERR_STACK = 1, ERR_PROGRESS = 2, ERR_ITER = 4 };
-
-template <int MODE> struct ValT { using T = float2; };
-template <> struct ValT<M_FP64> { using T = double2; };
-
-__device__ __forceinline__ double2 rot_v(double2 c, uint32_t k) { return rot_ik(c, k); }
-__device__ __forceinline__ float2 rot_v(float2 c, uint32_t k) { return rot_ikf(c, k); }
-__device__ __forceinline__ double2 mul_v(double2 a, double2 b) { return cmul(a, b); }
-__device__ __forceinline__ float2 mul_v(float2 a, float2 b) { return cmulf(a, b); }
-template <class V> __device__ __forceinline__ V one_v();
-template <> __device__ __forceinline__ double2 one_v<double2>() { return make_double2(1.0, 0.0); }
-template <> __device__ __forceinline__ float2 one_v<float2>() { return make_float2(1.f, 0.f); }
-
-// ---------------------------------------------------------------- record sources
-
-// Products of two sums: record r = j*na + i stands for a_i * b_j.
-//
-// When both operands are the same sum (sym != 0, e.g. H*H) only records with
-// i <= j exist.  P_a P_b and P_b P_a are the same string, and their phases
-// differ by 2*[a,b] (the symplectic inner product, Sec. III-D), so the pair
-// contributes i^k c_a c_b (1 + (-1)^[a,b]): twice one product when the
-// strings commute, exactly zero when they anti-commute.  The string is kept
-// either way, as in the ordered-pair form.
-template <int WP_, int MODE>
-struct ProdSrc {
-    static constexpr int WP = WP_;
-    static constexpr int NW = 2 * WP;
-    using V = typename ValT<MODE>::T;
-    const uint64_t* ak;
-    const uint64_t* bk;
-    const uint8_t* ap;
-    const uint8_t* bp;
-    const V* ac;
-    const V* bc;
-    uint32_t na;
-    uint32_t sym = 0;
-    __device__ __forceinline__ void split(uint32_t r, uint32_t& i, uint32_t& j) const {
-        j = r / na;
-        i = r - j * na;
-    }
-    __device__ __forceinline__ void key(uint32_t r, uint64_t (&k)[NW]) const {
-        uint32_t i, j;
-        split(r, i, j);
-        uint64_t a[NW], b[NW];
-        key_load_g<NW>(ak, i, a);
-        key_load_g<NW>(bk, j, b);
-#pragma unroll
-        for (int q = 0; q < NW; ++q) k[q] = a[q] ^ b[q];
-    }
-    // Product key, and the coefficient i^k c_a c_b in the mode's precision.
-    __device__ __forceinline__ V value(uint32_t r, uint64_t (&k)[NW]) const {
-        uint32_t i, j;
-        split(r, i, j);
-        uint64_t a[NW], b[NW];
-        key_load_g<NW>(ak, i, a);
-        key_load_g<NW>(bk, j, b);
-        const uint32_t ph = sym_flags(i, j, a, b) | string_product<WP>(a, b, __ldg(ap + i), __ldg(bp + j), k);
-        return apply(mul_v(ac[i], bc[j]), ph);
-    }
-    // Bit 2: the unordered pair cancels; bit 3: it counts twice.
-    __device__ __forceinline__ uint32_t sym_flags(uint32_t i, uint32_t j, const uint64_t (&a)[NW],
-                                                  const uint64_t (&b)[NW]) const {
-        if (!sym || i == j) return 0u;
-        uint64_t s = 0;
-#pragma unroll
-        for (int q = 0; q < WP; ++q) s ^= (a[q] & b[WP + q]) ^ (a[WP + q] & b[q]);
-        return (__popcll(s) & 1) ? 4u : 8u;
-    }
-    __device__ __forceinline__ V apply(V v, uint32_t ph) const {
-        if (ph & 4u) {
-            V z;
-            z.x = 0;
-            z.y = 0;
-            return z;
-        }
-        v = rot_v(v, ph & 3u);
-        if (ph & 8u) {
-            v.x += v.x;  // exact doubling
-            v.y += v.y;
-        }
-        return v;
-    }
-    // Product key and phase exponent (plus the symmetric-pair bits) only.
-    __device__ __forceinline__ uint32_t keyphase(uint32_t r, uint64_t (&k)[NW]) const {
-        uint32_t i, j;
-        split(r, i, j);
-        uint64_t a[NW], b[NW];
-        key_load_g<NW>(ak, i, a);
-        key_load_g<NW>(bk, j, b);
-        return sym_flags(i, j, a, b) | string_product<WP>(a, b, __ldg(ap + i), __ldg(bp + j), k);
-    }
-    // Coefficient of record r from its keyphase() bits.
-    __device__ __forceinline__ V coefv(uint32_t r, uint32_t ph) const {
-        uint32_t i, j;
-        split(r, i, j);
-        return apply(mul_v(ac[i], bc[j]), ph);
-    }
-};
-
-// Terms of one sum: record r is term r; value i^phase * c (or 1 when c is
-// null, which counts occurrences).
-template <int WP_, int MODE>
-struct TermSrc {
-    static constexpr int WP = WP_;
-    static constexpr int NW = 2 * WP;
-    using V = typename ValT<MODE>::T;
-    const uint64_t* keys;
-    const uint8_t* phase;
-    const V* c;
-    __device__ __forceinline__ void key(uint32_t r, uint64_t (&k)[NW]) const { key_load_g<NW>(keys, r, k); }
-    __device__ __forceinline__ V value(uint32_t r, uint64_t (&k)[NW]) const {
-        key_load_g<NW>(keys, r, k);
-        const V v = c ? c[r] : one_v<V>();
-        return rot_v(v, phase ? (uint32_t)(__ldg(phase + r) & 3u) : 0u);
-    }
-    __device__ __forceinline__ uint32_t keyphase(uint32_t r, uint64_t (&k)[NW]) const {
-        key_load_g<NW>(keys, r, k);
-        return phase ? (uint32_t)(__ldg(phase + r) & 3u) : 0u;
-    }
-    __device__ __forceinline__ V coefv(uint32_t r, uint32_t ph) const {
-        return rot_v(c ? c[r] : one_v<V>(), ph);
-    }
-};
-
-// Opaque NW-word keys with value 1 each: sorting them with the pipeline
-// yields the distinct keys and their multiplicities (used for splitters).
-template <int NW_>
-struct SampleSrc {
-    static constexpr int NW = NW_;
-    static constexpr int WP = NW_ / 2;
-    using V = double2;
-    const uint64_t* keys;
-    __device__ __forceinline__ void key(uint32_t r, uint64_t (&k)[NW]) const { key_load_g<NW>(keys, r, k); }
-    __device__ __forceinline__ V value(uint32_t r, uint64_t (&k)[NW]) const {
-        key_load_g<NW>(keys, r, k);
-        return make_double2(1.0, 0.0);
-    }
-    __device__ __forceinline__ uint32_t keyphase(uint32_t r, uint64_t (&k)[NW]) const {
-        key_load_g<NW>(keys, r, k);
-        return 0u;
-    }
-    __device__ __forceinline__ V coefv(uint32_t, uint32_t) const { return make_double2(1.0, 0.0); }
-};
-
-// ---------------------------------------------------------------- small helpers
-
-template <int NW>
-__device__ __forceinline__ bool key_succ(const uint64_t (&k)[NW], uint64_t (&o)[NW]) {
-    bool carry = true;
-#pragma unroll
-    for (int q = NW - 1; q >= 0; --q) {
-        o[q] = k[q] + (carry ? 1ull : 0ull);
-        carry = carry && (o[q] == 0ull);
-    }
-    return !carry;  // false on overflow (k was the largest key)
-}
-
-// Number of splitters <= k among n sorted splitters at `spl` (upper bound).
-template <int NW>
-__device__ __forceinline__ uint32_t upper_bound_keys(const uint64_t* spl, uint32_t n,
-                                                     const uint64_t (&k)[NW]) {
-    uint32_t lo = 0, len = n;
-    while (len > 0) {
-        const uint32_t half = len >> 1;
-        if (key_cmp_m<NW>(k, spl + (uint64_t)(lo + half) * NW) >= 0) {
-            lo += half + 1;
-            len -= half + 1;
-        } else {
-            len = half;
-        }
-    }
-    return lo;
-}
-
-// Keys held in shared memory are stored word-major: word w of key t at
-// s[w * stride + t].  Lanes that touch different keys then touch different
-// banks; a key-major layout (32- or 64-byte records) puts every lane on the
-// same few banks.
-template <int NW>
-__device__ __forceinline__ void skey_store(uint64_t* s, uint32_t stride, uint32_t t, const uint64_t (&k)[NW]) {
-#pragma unroll
-    for (int w = 0; w < NW; ++w) s[(size_t)w * stride + t] = k[w];
-}
-template <int NW>
-__device__ __forceinline__ void skey_load(const uint64_t* s, uint32_t stride, uint32_t t, uint64_t (&k)[NW]) {
-#pragma unroll
-    for (int w = 0; w < NW; ++w) k[w] = s[(size_t)w * stride + t];
-}
-template <int NW>
-__device__ __forceinline__ int skey_cmp(const uint64_t* s, uint32_t stride, uint32_t a, uint32_t b) {
-#pragma unroll 4
-    for (int w = 0; w < NW; ++w) {
-        const uint64_t u = s[(size_t)w * stride + a], v = s[(size_t)w * stride + b];
-        if (u != v) return u < v ? -1 : 1;
-    }
-    return 0;
-}
-template <int NW>
-__device__ __forceinline__ int skey_cmp_r(const uint64_t (&k)[NW], const uint64_t* s, uint32_t stride, uint32_t b) {
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        const uint64_t v = s[(size_t)w * stride + b];
-        if (k[w] != v) return k[w] < v ? -1 : 1;
-    }
-    return 0;
-}
-// Number of splitters <= k among n sorted word-major splitters.
-template <int NW>
-__device__ __forceinline__ uint32_t upper_bound_skeys(const uint64_t* s, uint32_t stride, uint32_t n,
-                                                      const uint64_t (&k)[NW]) {
-    uint32_t lo = 0, len = n;
-    while (len > 0) {
-        const uint32_t half = len >> 1;
-        if (skey_cmp_r<NW>(k, s, stride, lo + half) >= 0) {
-            lo += half + 1;
-            len -= half + 1;
-        } else {
-            len = half;
-        }
-    }
-    return lo;
-}
-
-template <int THREADS>
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp, uint32_t& total) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        uint32_t w = lane < THREADS / 32 ? s_warp[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < THREADS / 32) s_warp[lane] = w;
-    }
-    __syncthreads();
-    total = s_warp[THREADS / 32 - 1];
-    const uint32_t before = wid ? s_warp[wid - 1] : 0u;
-    __syncthreads();
-    return before + x - v;
-}
-
-// ---------------------------------------------------------------- accumulators
-
-template <int MODE> struct Acc;
-template <> struct Acc<M_FP64> {
-    double re = 0.0, im = 0.0;
-    __device__ __forceinline__ void add(double2 v) { re += v.x; im += v.y; }
-    __device__ __forceinline__ void merge(const Acc& o) { re += o.re; im += o.im; }
-    __device__ __forceinline__ double2 result() const { return make_double2(re, im); }
-    __device__ __forceinline__ void shfl_merge(int o) {
-        Acc t;
-        t.re = __shfl_down_sync(0xffffffffu, re, o);
-        t.im = __shfl_down_sync(0xffffffffu, im, o);
-        merge(t);
-    }
-};
-template <> struct Acc<M_F32_D64> {
-    double re = 0.0, im = 0.0;
-    __device__ __forceinline__ void add(float2 v) { re += (double)v.x; im += (double)v.y; }
-    __device__ __forceinline__ void merge(const Acc& o) { re += o.re; im += o.im; }
-    __device__ __forceinline__ double2 result() const { return make_double2(re, im); }
-    __device__ __forceinline__ void shfl_merge(int o) {
-        Acc t;
-        t.re = __shfl_down_sync(0xffffffffu, re, o);
-        t.im = __shfl_down_sync(0xffffffffu, im, o);
-        merge(t);
-    }
-};
-// FP32 sum with TwoSum error terms (Ogita, Rump, Oishi 2005, Sum2): the
-// rounding error of every addition is collected exactly and added back once.
-template <> struct Acc<M_F32_TWOSUM> {
-    float sr = 0.f, er = 0.f, si = 0.f, ei = 0.f;
-    __device__ __forceinline__ void add(float2 v) {
-        float s, e;
-        two_sum(sr, v.x, s, e);
-        sr = s;
-        er = __fadd_rn(er, e);
-        two_sum(si, v.y, s, e);
-        si = s;
-        ei = __fadd_rn(ei, e);
-    }
-    __device__ __forceinline__ void merge(const Acc& o) {
-        float s, e;
-        two_sum(sr, o.sr, s, e);
-        sr = s;
-        er = __fadd_rn(__fadd_rn(er, o.er), e);
-        two_sum(si, o.si, s, e);
-        si = s;
-        ei = __fadd_rn(__fadd_rn(ei, o.ei), e);
-    }
-    __device__ __forceinline__ double2 result() const {
-        return make_double2((double)sr + (double)er, (double)si + (double)ei);
-    }
-    __device__ __forceinline__ void shfl_merge(int o) {
-        Acc t;
-        t.sr = __shfl_down_sync(0xffffffffu, sr, o);
-        t.er = __shfl_down_sync(0xffffffffu, er, o);
-        t.si = __shfl_down_sync(0xffffffffu, si, o);
-        t.ei = __shfl_down_sync(0xffffffffu, ei, o);
-        merge(t);
-    }
-};
-
-// ---------------------------------------------------------------- capacities
-
-constexpr int kL2Threads = 512;
-constexpr int kStackCap = 4096;
-constexpr int kSmemBudget = 110 * 1024;
-
-// Shared memory per leaf record: the product key (8*NW bytes), a packed sort
-// code (8 bytes), the record number (4 bytes, the tie-break that makes the
-// order of equal keys and so the summation order deterministic) and the
-// product's phase exponent (1 byte).  At most 4096 records, so a slot number
-// fits the code's low 12 bits.
-constexpr int kLeafRecBytes = 8 + 4 + 1;
-template <int NW>
-constexpr int leaf_cap() {
-    int cap = 4096;
-    while (cap > 64 && cap * (8 * NW + kLeafRecBytes) > kSmemBudget) cap >>= 1;
-    return cap;
-}
-template <int NW>
-constexpr size_t leaf_smem() {
-    return (size_t)leaf_cap<NW>() * (8 * NW + kLeafRecBytes);
-}
-
-// Coarse (level 1) splitters live in shared memory of the counting kernel.
-template <int NW>
-constexpr int max_coarse_splitters() {
-    return (128 * 1024) / (8 * NW) < 4094 ? (128 * 1024) / (8 * NW) : 4094;
-}
-
-// ---------------------------------------------------------------- sampling
-
-template <class Src>
-struct IsProdT : std::false_type {};
-template <int WP, int MODE>
-struct IsProdT<ProdSrc<WP, MODE>> : std::true_type {};
-
-template <class Src>
-__global__ void k_sample(Src src, uint32_t R, uint32_t S, uint64_t seed, uint64_t* out) {
-    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    uint32_t r;
-    if (S >= R) r = s;
-    else r = (uint32_t)(mix64(seed + s) % R);
-    if constexpr (IsProdT<Src>::value) {
-        if (src.sym) {  // fold onto the i <= j triangle
-            const uint32_t j = r / src.na, i = r - j * src.na;
-            if (i > j) r = i * src.na + j;
-        }
-    }
-    uint64_t k[Src::NW];
-    src.key(r, k);
-    key_store<Src::NW>(out, s, k);
-}
-
-// One coarse range holding every record in order.
-__global__ void k_iota(uint32_t* rec, uint32_t n, uint64_t* boff, uint8_t* bflags) {
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) rec[t] = t;
-    if (t == 0) {
-        boff[0] = 0;
-        boff[1] = n;
-        bflags[0] = 0;
-    }
-}
-
-// One coarse range holding the i <= j records of a symmetric product, in
-// order: t -> (i, j) with j(j+1)/2 <= t < (j+1)(j+2)/2.
-__global__ void k_iota_tri(uint32_t* rec, uint32_t n, uint32_t na, uint64_t* boff, uint8_t* bflags) {
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) {
-        uint64_t j = (uint64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-        while (j * (j + 1) / 2 > t) --j;
-        while ((j + 1) * (j + 2) / 2 <= t) ++j;
-        const uint64_t i = t - j * (j + 1) / 2;
-        rec[t] = (uint32_t)(j * na + i);
-    }
-    if (t == 0) {
-        boff[0] = 0;
-        boff[1] = n;
-        bflags[0] = 0;
-    }
-}
-
-// Splitter choice from the sorted, merged sample: keys dk[u] with occurrence
-// counts dc[u].x.  For t = 1..B1-1 the key holding sample rank t*S/B1 gives
-// a pair (key, succ(key)) when that key fills at least one whole coarse
-// range (a uniform range), else (key, key) (an empty range).
-template <int NW>
-__global__ void __launch_bounds__(1024) k_select(const uint64_t* __restrict__ dk,
-                                                 const double2* __restrict__ dc,
-                                                 const uint64_t* __restrict__ u_dev, uint32_t S,
-                                                 uint32_t B1, uint32_t* pref, uint64_t* spl,
-                                                 uint8_t* bflags) {
-    __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_carry;
-    const uint32_t U = (uint32_t)*u_dev;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (uint32_t base = 0; base < U; base += 1024) {
-        const uint32_t u = base + threadIdx.x;
-        const uint32_t c = u < U ? (uint32_t)dc[u].x : 0u;
-        uint32_t total;
-        const uint32_t ex = block_excl_scan<1024>(c, s_warp, total);
-        if (u < U) pref[u] = s_carry + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += total;
-        __syncthreads();
-    }
-    const uint32_t nb = 2 * B1 - 1;
-    for (uint32_t b = threadIdx.x; b < nb; b += 1024) bflags[b] = 0;
-    __syncthreads();
-    const double full = (double)S / (double)B1;
-    for (uint32_t t = 1 + threadIdx.x; t < B1; t += 1024) {
-        const uint32_t tau = (uint32_t)(((uint64_t)t * S) / B1);
-        // largest u with pref[u] <= tau
-        uint32_t lo = 0, hi = U;  // pref[lo] <= tau invariant (pref[0] = 0)
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (pref[mid] <= tau) lo = mid; else hi = mid;
-        }
-        uint64_t k[NW], s2[NW];
-        key_load_g<NW>(dk, lo, k);
-        const bool heavy = dc[lo].x >= full;
-        bool ok = true;
-        if (heavy) ok = key_succ<NW>(k, s2);
-        key_store<NW>(spl, 2 * (t - 1), k);
-        if (heavy && ok) {
-            key_store<NW>(spl, 2 * (t - 1) + 1, s2);
-            bflags[2 * t - 1] = 1;
-        } else {
-            key_store<NW>(spl, 2 * (t - 1) + 1, k);
-            if (heavy) bflags[nb - 1] = 1;  // the largest possible key: its range is the last one
-        }
-    }
-}
-
-// ---------------------------------------------------------------- level 1: count
-
-constexpr int kCountThreads = 256;
-constexpr int kCountCols = 64;
-
-// Products: a tile is kCountThreads left terms x kCountCols right terms.
-template <int WP, int MODE>
-__global__ void __launch_bounds__(kCountThreads) k_count_prod(ProdSrc<WP, MODE> src, uint32_t nb_terms,
-                                                               const uint64_t* __restrict__ spl,
-                                                               uint32_t nsp, uint16_t* ids,
-                                                               uint32_t* counts) {
-    constexpr int NW = 2 * WP;
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* s_spl = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* s_b = s_spl + (size_t)nsp * NW;
-    uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_b + kCountCols * NW);
-    const uint32_t nbk = nsp + 1;
-    for (uint32_t q = threadIdx.x; q < nsp * NW; q += blockDim.x) s_spl[(q % NW) * nsp + q / NW] = spl[q];
-    for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x) s_hist[q] = 0;
-    const uint32_t na = src.na;
-    const uint32_t ti_n = (na + kCountThreads - 1) / kCountThreads;
-    const uint32_t tj_n = (nb_terms + kCountCols - 1) / kCountCols;
-    const uint64_t ntiles = (uint64_t)ti_n * tj_n;
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint32_t ti = (uint32_t)(tile % ti_n), tj = (uint32_t)(tile / ti_n);
-        const uint32_t j0 = tj * kCountCols;
-        const uint32_t ncols = min((uint32_t)kCountCols, nb_terms - j0);
-        __syncthreads();
-        for (uint32_t q = threadIdx.x; q < ncols * NW; q += blockDim.x) s_b[q] = src.bk[(uint64_t)j0 * NW + q];
-        __syncthreads();
-        const uint32_t i = ti * kCountThreads + threadIdx.x;
-        if (i < na) {
-            uint64_t a[NW];
-            key_load_g<NW>(src.ak, i, a);
-            for (uint32_t c = 0; c < ncols; ++c) {
-                if (src.sym && i > j0 + c) continue;  // the (j, i) record stands for both orders
-                uint64_t k[NW];
-                const uint64_t* bb = s_b + c * NW;
-#pragma unroll
-                for (int q = 0; q < NW; ++q) k[q] = a[q] ^ bb[q];
-                const uint32_t bkt = upper_bound_skeys<NW>(s_spl, nsp, nsp, k);
-                ids[(uint64_t)(j0 + c) * na + i] = (uint16_t)bkt;
-                atomicAdd(&s_hist[bkt], 1u);
-            }
-        }
-    }
-    __syncthreads();
-    for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x)
-        if (s_hist[q]) atomicAdd(&counts[q], s_hist[q]);
-}
-
-template <class Src>
-__global__ void __launch_bounds__(kCountThreads) k_count_lin(Src src, uint32_t R,
-                                                              const uint64_t* __restrict__ spl,
-                                                              uint32_t nsp, uint16_t* ids,
-                                                              uint32_t* counts) {
-    constexpr int NW = Src::NW;
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* s_spl = reinterpret_cast<uint64_t*>(smem);
-    uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_spl + (size_t)nsp * NW);
-    const uint32_t nbk = nsp + 1;
-    for (uint32_t q = threadIdx.x; q < nsp * NW; q += blockDim.x) s_spl[(q % NW) * nsp + q / NW] = spl[q];
-    for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x) s_hist[q] = 0;
-    __syncthreads();
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
-        uint64_t k[NW];
-        src.key(r, k);
-        const uint32_t bkt = upper_bound_skeys<NW>(s_spl, nsp, nsp, k);
-        ids[r] = (uint16_t)bkt;
-        atomicAdd(&s_hist[bkt], 1u);
-    }
-    __syncthreads();
-    for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x)
-        if (s_hist[q]) atomicAdd(&counts[q], s_hist[q]);
-}
-
-// Exclusive scan of n 32-bit counts into 64-bit offsets (single CTA).
-__global__ void __launch_bounds__(1024) k_scan_counts(const uint32_t* __restrict__ cnt, uint32_t n,
-                                                      uint64_t* off) {
-    __shared__ uint32_t s_warp[32];
-    __shared__ uint64_t s_carry;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (uint32_t base = 0; base < n; base += 1024) {
-        const uint32_t u = base + threadIdx.x;
-        const uint32_t c = u < n ? cnt[u] : 0u;
-        uint32_t total;
-        const uint32_t ex = block_excl_scan<1024>(c, s_warp, total);
-        if (u < n) off[u] = s_carry + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += total;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) off[n] = s_carry;
-}
-
-__global__ void __launch_bounds__(1024) k_scan_u64(const uint64_t* __restrict__ cnt, uint32_t n,
-                                                   uint64_t* off) {
-    __shared__ uint64_t s_v[1024];
-    __shared__ uint64_t s_carry;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (uint32_t base = 0; base < n; base += 1024) {
-        const uint32_t u = base + threadIdx.x;
-        uint64_t v = u < n ? cnt[u] : 0ull;
-        s_v[threadIdx.x] = v;
-        __syncthreads();
-        for (int o = 1; o < 1024; o <<= 1) {
-            const uint64_t y = threadIdx.x >= (uint32_t)o ? s_v[threadIdx.x - o] : 0ull;
-            __syncthreads();
-            s_v[threadIdx.x] += y;
-            __syncthreads();
-        }
-        if (u < n) off[u] = s_carry + s_v[threadIdx.x] - v;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += s_v[1023];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) off[n] = s_carry;
-}
-
-// ---------------------------------------------------------------- level 1: scatter
-
-constexpr int kScatterThreads = 512;
-constexpr uint32_t kScatterChunk = 32768;
-
-__global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint16_t* __restrict__ ids, uint32_t R,
-                                                             uint32_t nbk, uint64_t* cursor,
-                                                             uint32_t* rec, uint32_t sym_na) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);
-    uint64_t* s_base = reinterpret_cast<uint64_t*>(s_cnt + ((nbk + 1) & ~1u));
-    for (uint64_t c0 = (uint64_t)blockIdx.x * kScatterChunk; c0 < R; c0 += (uint64_t)gridDim.x * kScatterChunk) {
-        const uint32_t c1 = (uint32_t)mn<uint64_t>(R, c0 + kScatterChunk);
-        __syncthreads();
-        for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x) s_cnt[q] = 0;
-        __syncthreads();
-        for (uint32_t r = (uint32_t)c0 + threadIdx.x; r < c1; r += blockDim.x) {
-            if (sym_na && r % sym_na > r / sym_na) continue;  // no record for i > j
-            atomicAdd(&s_cnt[ids[r]], 1u);
-        }
-        __syncthreads();
-        for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x) {
-            const uint32_t c = s_cnt[q];
-            s_base[q] = c ? atomicAdd(reinterpret_cast<unsigned long long*>(cursor + q), (unsigned long long)c) : 0ull;
-            s_cnt[q] = 0;
-        }
-        __syncthreads();
-        for (uint32_t r = (uint32_t)c0 + threadIdx.x; r < c1; r += blockDim.x) {
-            if (sym_na && r % sym_na > r / sym_na) continue;
-            const uint32_t b = ids[r];
-            const uint32_t p = atomicAdd(&s_cnt[b], 1u);
-            rec[s_base[b] + p] = r;
-        }
-    }
-}
-
-// ---------------------------------------------------------------- level 2
-
-struct StackEnt {
-    uint32_t lo, hi, flags, pad;
-};
-enum : uint32_t { SF_UNIFORM = 1u, SF_INB = 2u };
-
-template <class Src, int MODE>
-struct L2Cfg {
-    using V = typename Src::V;
-    static constexpr int NW = Src::NW;
-    static constexpr int CAP = leaf_cap<NW>();
-    static constexpr size_t SMEM = leaf_smem<NW>();
-};
-
-// Order of two packed sort codes.  A code holds, above bit 12, the 52 key
-// bits that follow the common prefix of every key in the range, and the
-// element's slot below.  Equal upper bits fall back to the full keys, then to
-// the record number; slots >= n are padding that sorts last.
-template <int NW, uint32_t CAP>
-__device__ __forceinline__ bool code_gt(uint64_t a, uint64_t b, const uint64_t* keys_s, uint32_t n,
-                                        const uint32_t* recs, uint32_t lo) {
-    if ((a ^ b) >> 12) return a > b;
-    const uint32_t ia = (uint32_t)(a & 0xFFFu), ib = (uint32_t)(b & 0xFFFu);
-    if (ia >= n || ib >= n) return ia >= n && (ib < n || ia > ib);
-    const int c = skey_cmp<NW>(keys_s, CAP, ia, ib);
-    if (c) return c > 0;
-    if (recs) return recs[ia] > recs[ib];
-    return ia > ib;
-}
-
-template <int NW, uint32_t CAP>
-__device__ __forceinline__ bool code_key_neq(uint64_t a, uint64_t b, const uint64_t* keys_s) {
-    if ((a ^ b) >> 12) return true;
-    return skey_cmp<NW>(keys_s, CAP, (uint32_t)(a & 0xFFFu), (uint32_t)(b & 0xFFFu)) != 0;
-}
-
-// Packed codes for keys_s[0..n): the first bit position L where any key
-// differs from key 0 is found with an OR reduction; each code then takes the
-// 52 bits starting at L.  Slots [n, p2) get padding codes.
-template <int NW, int T, uint32_t CAP>
-__device__ void build_codes(uint64_t* code_s, const uint64_t* keys_s, uint32_t n, uint32_t p2,
-                            unsigned long long* s_or, uint32_t* s_L) {
-    for (int w = threadIdx.x; w < NW; w += T) s_or[w] = 0ull;
-    __syncthreads();
-    uint64_t acc[NW];
-#pragma unroll
-    for (int w = 0; w < NW; ++w) acc[w] = 0;
-    for (uint32_t t = threadIdx.x; t < n; t += T) {
-#pragma unroll
-        for (int w = 0; w < NW; ++w) acc[w] |= keys_s[(size_t)w * CAP + t] ^ keys_s[(size_t)w * CAP];
-    }
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        uint64_t v = acc[w];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0 && v) atomicOr(&s_or[w], (unsigned long long)v);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t L = 64u * NW;
-        for (int w = 0; w < NW; ++w)
-            if (s_or[w]) { L = 64u * w + (uint32_t)__clzll((long long)s_or[w]); break; }
-        *s_L = L;
-    }
-    __syncthreads();
-    const uint32_t L = *s_L;
-    const uint32_t w0 = L >> 6, sh = L & 63u;
-    for (uint32_t t = threadIdx.x; t < p2; t += T) {
-        uint64_t code;
-        if (t >= n) {
-            code = ~0xFFFull | t;
-        } else if (w0 >= (uint32_t)NW) {
-            code = t;
-        } else {
-            uint64_t hi = keys_s[(size_t)w0 * CAP + t] << sh;
-            if (sh && w0 + 1 < (uint32_t)NW) hi |= keys_s[(size_t)(w0 + 1) * CAP + t] >> (64u - sh);
-            code = (hi & ~0xFFFull) | t;
-        }
-        code_s[t] = code;
-    }
-    __syncthreads();
-}
-
-template <int NW, int T, uint32_t CAP>
-__device__ void block_sort_codes(uint64_t* code_s, const uint64_t* keys_s, uint32_t n, uint32_t p2,
-                                 const uint32_t* recs, uint32_t lo) {
-    for (uint32_t kk = 2; kk <= p2; kk <<= 1) {
-        for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
-            for (uint32_t t = threadIdx.x; t < p2 / 2; t += T) {
-                const uint32_t i = 2 * t - (t & (jj - 1));
-                const uint32_t l = i + jj;
-                const uint64_t a = code_s[i], b = code_s[l];
-                const bool up = (i & kk) == 0;
-                if (code_gt<NW, CAP>(a, b, keys_s, n, recs, lo) == up) {
-                    code_s[i] = b;
-                    code_s[l] = a;
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
-template <class Src, int MODE>
-__global__ void __launch_bounds__(kL2Threads) k_level2(
-    Src src, uint32_t nbk, const uint64_t* __restrict__ boff, const uint8_t* __restrict__ bflags,
-    uint32_t* recA, uint32_t* recB, uint16_t* subid, uint32_t* ticket, StackEnt* stacks,
-    uint64_t* spl_scratch, uint64_t* Tkeys, double2* Tcoef, uint64_t* ucount, int32_t* err) {
-    using Cfg = L2Cfg<Src, MODE>;
-    constexpr int NW = Cfg::NW;
-    constexpr uint32_t CAP = Cfg::CAP;
-    constexpr int T = kL2Threads;
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* keys_s = reinterpret_cast<uint64_t*>(smem);                     // [NW][CAP]
-    uint64_t* code_s = keys_s + (size_t)CAP * NW;                             // [CAP]
-    uint32_t* rec_s = reinterpret_cast<uint32_t*>(code_s + CAP);              // [CAP]
-    uint8_t* ph_s = reinterpret_cast<uint8_t*>(rec_s + CAP);                  // [CAP]
-    __shared__ uint32_t s_warp[32];
-    __shared__ unsigned long long s_or[NW];
-    __shared__ uint32_t s_bucket, s_lo, s_hi, s_fl, s_sp, s_done, s_nsp, s_bad, s_L;
-    __shared__ uint64_t s_u, s_tbase;
-
-    StackEnt* stack = stacks + (size_t)blockIdx.x * kStackCap;
-    uint64_t* my_spl = spl_scratch + (size_t)blockIdx.x * (CAP / 2) * NW;
-    const int tid = threadIdx.x;
-
-    for (;;) {
-        if (tid == 0) s_bucket = atomicAdd(ticket, 1u);
-        __syncthreads();
-        const uint32_t c = s_bucket;
-        if (c >= nbk) break;
-        const uint64_t base0 = boff[c];
-        const uint64_t end0 = boff[c + 1];
-        if (tid == 0) {
-            s_u = 0;
-            s_tbase = base0;
-            s_bad = 0;
-            s_sp = 0;
-            if (end0 > base0) {
-                stack[0] = StackEnt{(uint32_t)base0, (uint32_t)end0, bflags[c] ? SF_UNIFORM : 0u, 0u};
-                s_sp = 1;
-            }
-        }
-        __syncthreads();
-        uint32_t iters = 0;
-        for (;;) {
-            if (tid == 0) {
-                if (s_sp == 0 || s_bad) {
-                    s_done = 1;
-                } else {
-                    const StackEnt e = stack[--s_sp];
-                    s_lo = e.lo;
-                    s_hi = e.hi;
-                    s_fl = e.flags;
-                    s_done = 0;
-                }
-            }
-            __syncthreads();
-            if (s_done) break;
-            if (++iters > (1u << 24)) {
-                if (tid == 0) { atomicOr(err, ERR_ITER); s_bad = 1; }
-                __syncthreads();
-                break;
-            }
-            const uint32_t lo = s_lo, hi = s_hi, fl = s_fl;
-            const uint32_t n = hi - lo;
-            const uint64_t tout = s_tbase + s_u;
-            uint32_t* cur = (fl & SF_INB) ? recB : recA;
-            uint32_t* oth = (fl & SF_INB) ? recA : recB;
-
-            if (fl & SF_UNIFORM) {
-                // ---- every record in the range has the same key
-                Acc<MODE> acc;
-                for (uint32_t t = tid; t < n; t += T) {
-                    uint64_t k[NW];
-                    acc.add(src.value(cur[lo + t], k));
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc.shfl_merge(o);
-                Acc<MODE>* s_acc = reinterpret_cast<Acc<MODE>*>(code_s);
-                if ((tid & 31) == 0) s_acc[tid >> 5] = acc;
-                __syncthreads();
-                if (tid < 32) {
-                    Acc<MODE> a2;
-                    if (tid < T / 32) a2 = s_acc[tid];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) a2.shfl_merge(o);
-                    if (tid == 0) {
-                        uint64_t k[NW];
-                        src.key(cur[lo], k);
-                        key_store<NW>(Tkeys, tout, k);
-                        Tcoef[tout] = a2.result();
-                        s_u += 1;
-                    }
-                }
-                __syncthreads();
-            } else if (n <= CAP) {
-                // ---- leaf: product keys and phases into shared memory, sort
-                // by (key, record), then sum each run of equal keys
-                for (uint32_t t = tid; t < n; t += T) {
-                    uint64_t k[NW];
-                    const uint32_t r = cur[lo + t];
-                    rec_s[t] = r;
-                    ph_s[t] = (uint8_t)src.keyphase(r, k);
-                    skey_store<NW>(keys_s, CAP, t, k);
-                }
-                uint32_t p2 = 1;
-                while (p2 < n) p2 <<= 1;
-                __syncthreads();
-                build_codes<NW, T, CAP>(code_s, keys_s, n, p2, s_or, &s_L);
-                block_sort_codes<NW, T, CAP>(code_s, keys_s, n, p2, rec_s, 0);
-                constexpr uint32_t IPT = (CAP + T - 1) / T;
-                const uint32_t p0 = tid * IPT;
-                const uint32_t p1 = min(n, p0 + IPT);
-                uint32_t my_heads = 0;
-                for (uint32_t p = p0; p < p1; ++p)
-                    if (p == 0 || code_key_neq<NW, CAP>(code_s[p], code_s[p - 1], keys_s)) ++my_heads;
-                uint32_t total;
-                uint32_t hidx = block_excl_scan<T>(my_heads, s_warp, total);
-                for (uint32_t p = p0; p < p1; ++p) {
-                    const uint64_t hc = code_s[p];
-                    if (p == 0 || code_key_neq<NW, CAP>(hc, code_s[p - 1], keys_s)) {
-                        Acc<MODE> acc;
-                        uint32_t q = p;
-                        do {
-                            const uint32_t idx = (uint32_t)(code_s[q] & 0xFFFu);
-                            acc.add(src.coefv(rec_s[idx], ph_s[idx]));
-                            ++q;
-                        } while (q < n && !code_key_neq<NW, CAP>(hc, code_s[q], keys_s));
-                        uint64_t k[NW];
-                        skey_load<NW>(keys_s, CAP, (uint32_t)(hc & 0xFFFu), k);
-                        key_store<NW>(Tkeys, tout + hidx, k);
-                        Tcoef[tout + hidx] = acc.result();
-                        ++hidx;
-                    }
-                }
-                __syncthreads();
-                if (tid == 0) s_u += total;
-                __syncthreads();
-            } else {
-                // ---- split: splitters from a sorted sample of this range
-                const uint32_t S = CAP;
-                for (uint32_t t = tid; t < S; t += T) {
-                    const uint32_t pos = lo + (uint32_t)(((uint64_t)t * n) / S);
-                    uint64_t k[NW];
-                    src.key(cur[pos], k);
-                    skey_store<NW>(keys_s, CAP, t, k);
-                }
-                __syncthreads();
-                build_codes<NW, T, CAP>(code_s, keys_s, S, S, s_or, &s_L);
-                block_sort_codes<NW, T, CAP>(code_s, keys_s, S, S, nullptr, 0);
-                const uint32_t want = (uint32_t)mn<uint64_t>(CAP / 4, ((uint64_t)n + CAP / 2 - 1) / (CAP / 2));
-                uint8_t* fl_s = ph_s;  // flag of range b+1 follows splitter b
-                if (tid == 0) {
-                    uint32_t nsp = 0;
-                    fl_s[0] = 0;
-                    bool stop = false;
-                    for (uint32_t t = 1; t < want && !stop; ++t) {
-                        const uint32_t rho = (uint32_t)(((uint64_t)t * S) / want);
-                        const uint32_t ci = (uint32_t)(code_s[rho] & 0xFFFu);
-                        uint64_t k[NW], s2[NW];
-                        skey_load<NW>(keys_s, CAP, ci, k);
-                        if (nsp > 0 && key_cmp_m<NW>(k, my_spl + (size_t)(nsp - 1) * NW) <= 0) continue;
-                        const bool heavy =
-                            (rho > 0 && skey_cmp<NW>(keys_s, CAP, ci, (uint32_t)(code_s[rho - 1] & 0xFFFu)) == 0) ||
-                            (rho + 1 < S && skey_cmp<NW>(keys_s, CAP, ci, (uint32_t)(code_s[rho + 1] & 0xFFFu)) == 0);
-                        key_store<NW>(my_spl, nsp, k);
-                        ++nsp;
-                        fl_s[nsp] = heavy ? 1u : 0u;
-                        if (heavy) {
-                            if (key_succ<NW>(k, s2)) {
-                                key_store<NW>(my_spl, nsp, s2);
-                                ++nsp;
-                                fl_s[nsp] = 0;
-                            } else {
-                                stop = true;  // nothing sorts after the largest key
-                            }
-                        }
-                    }
-                    s_nsp = nsp;
-                }
-                __syncthreads();
-                const uint32_t nsp = s_nsp;
-                const uint32_t nbs = nsp + 1;
-                for (uint32_t q = tid; q < nsp * NW; q += T) keys_s[(q % NW) * (CAP / 2) + q / NW] = my_spl[q];
-                uint32_t* cnt = reinterpret_cast<uint32_t*>(code_s);  // [nbs]
-                uint32_t* cpos = cnt + CAP / 2;                         // [nbs]
-                for (uint32_t q = tid; q < nbs; q += T) { cnt[q] = 0; cpos[q] = 0; }
-                __syncthreads();
-                for (uint32_t idx = lo + tid; idx < hi; idx += T) {
-                    uint64_t k[NW];
-                    src.key(cur[idx], k);
-                    const uint32_t b = upper_bound_skeys<NW>(keys_s, CAP / 2, nsp, k);
-                    subid[idx] = (uint16_t)b;
-                    atomicAdd(&cnt[b], 1u);
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    uint32_t run = 0;
-                    uint32_t bad = 0;
-                    for (uint32_t b = 0; b < nbs; ++b) {
-                        const uint32_t cb = cnt[b];
-                        if (cb == n && !(fl_s[b] & 1u)) bad = 1;  // no progress
-                        cnt[b] = run;
-                        run += cb;
-                    }
-                    if (bad) { atomicOr(err, ERR_PROGRESS); s_bad = 1; }
-                    else if (s_sp + nbs > (uint32_t)kStackCap) { atomicOr(err, ERR_STACK); s_bad = 1; }
-                }
-                __syncthreads();
-                if (!s_bad) {
-                    for (uint32_t idx = lo + tid; idx < hi; idx += T) {
-                        const uint32_t b = subid[idx];
-                        const uint32_t p = atomicAdd(&cpos[b], 1u);
-                        oth[lo + cnt[b] + p] = cur[idx];
-                    }
-                    __syncthreads();
-                    if (tid == 0) {
-                        const uint32_t inb = (fl & SF_INB) ? 0u : SF_INB;  // children live in the other buffer
-                        for (int b = (int)nbs - 1; b >= 0; --b) {
-                            const uint32_t s0 = cnt[b];
-                            const uint32_t s1 = (b + 1 < (int)nbs) ? cnt[b + 1] : n;
-                            if (s1 > s0)
-                                stack[s_sp++] = StackEnt{lo + s0, lo + s1, ((fl_s[b] & 1u) ? SF_UNIFORM : 0u) | inb, 0u};
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        if (tid == 0) ucount[c] = s_u;
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------- compaction
-
-template <int WP>
-__global__ void __launch_bounds__(256) k_compact(uint32_t nbk, const uint64_t* __restrict__ boff,
-                                                 const uint64_t* __restrict__ uoff,
-                                                 const uint64_t* __restrict__ Tkeys,
-                                                 const double2* __restrict__ Tcoef, uint64_t* okeys,
-                                                 double2* ocoef, uint8_t* opb) {
-    constexpr int NW = 2 * WP;
-    for (uint32_t c = blockIdx.x; c < nbk; c += gridDim.x) {
-        const uint64_t src0 = boff[c];
-        const uint64_t dst0 = uoff[c];
-        const uint64_t cnt = uoff[c + 1] - dst0;
-        for (uint64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
-            uint64_t k[NW];
-            key_load_g<NW>(Tkeys, src0 + t, k);
-            key_store<NW>(okeys, dst0 + t, k);
-            ocoef[dst0 + t] = Tcoef[src0 + t];
-            opb[dst0 + t] = (uint8_t)normal_phase<WP>(k, 0u);
-        }
-    }
-}
-
-// Copies compacted (key, coefficient) pairs into dense scratch arrays (used
-// for the merged sample inside splitter selection).
-template <int NW>
-__global__ void k_compact_plain(uint32_t nbk, const uint64_t* __restrict__ boff,
-                                const uint64_t* __restrict__ uoff, const uint64_t* __restrict__ Tkeys,
-                                const double2* __restrict__ Tcoef, uint64_t* okeys, double2* ocoef) {
-    for (uint32_t c = blockIdx.x; c < nbk; c += gridDim.x) {
-        const uint64_t src0 = boff[c];
-        const uint64_t dst0 = uoff[c];
-        const uint64_t cnt = uoff[c + 1] - dst0;
-        for (uint64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
-            uint64_t k[NW];
-            key_load_g<NW>(Tkeys, src0 + t, k);
-            key_store<NW>(okeys, dst0 + t, k);
-            ocoef[dst0 + t] = Tcoef[src0 + t];
-        }
-    }
-}
-
-template <int MODE>
-__global__ void k_to_f32(const double2* __restrict__ in, float2* out, int64_t n) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) out[t] = make_float2(__double2float_rn(in[t].x), __double2float_rn(in[t].y));
-}
-
-// ---------------------------------------------------------------- host pipeline
-
-// Opt a kernel into more than 48 KB of dynamic shared memory.  Attributes
-// persist, so a capture-safe (replayed) launch skips the call.
-template <class F>
-static void smem_attr(F* kern, size_t bytes) {
-    if (capture_safe()) return;
-    check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes), "attr");
-}
-
-__global__ void k_or_err(const int32_t* inner, int32_t* outer) {
-    if (threadIdx.x == 0 && *inner) atomicOr(outer, *inner);
-}
-
-struct Staged {
-    // merged terms of every coarse range, dense within [boff[c], boff[c] + U_c)
-    Scratch Tkeys, Tcoef, boff, uoff, err;
-    uint32_t nbk = 0;
-};
-
-template <class Src>
-struct IsProd : std::false_type {};
-template <int WP, int MODE>
-struct IsProd<ProdSrc<WP, MODE>> : std::true_type {};
-
-static uint64_t g_sample_seed = 0x5eed5eedull;
-
-template <class Src, int MODE>
-static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStream_t st, Staged& out);
-
-// Sorted distinct sample keys with their multiplicities.
-template <int NW>
-static void sorted_sample(const uint64_t* samp, uint32_t S, cudaStream_t st, Scratch& dk, Scratch& dc,
-                          Scratch& du, int32_t* outer_err) {
-    SampleSrc<NW> ts{samp};
-    Staged sg;
-    run_pipeline<SampleSrc<NW>, M_FP64>(ts, S, 0, st, sg);
-    dk = Scratch((size_t)S * NW * 8, st);
-    dc = Scratch((size_t)S * 16, st);
-    du = Scratch(8, st);
-    note_launch(ST_SAMPLE);
-    k_compact_plain<NW><<<std::min<uint32_t>(sg.nbk, 1024), 256, 0, st>>>(
-        sg.nbk, sg.boff.as<uint64_t>(), sg.uoff.as<uint64_t>(), sg.Tkeys.as<uint64_t>(),
-        sg.Tcoef.as<double2>(), dk.as<uint64_t>(), dc.as<double2>());
-    check_cuda(cudaMemcpyAsync(du.p, sg.uoff.as<uint64_t>() + sg.nbk, 8, cudaMemcpyDeviceToDevice, st),
-               "sample count copy");
-    check_cuda(cudaGetLastError(), "sample compaction");
-    // the inner pipeline's error word joins the caller's (no host sync)
-    k_or_err<<<1, 32, 0, st>>>(sg.err.as<int32_t>(), outer_err);
-    check_cuda(cudaGetLastError(), "k_or_err");
-}
-
-template <class Src, int MODE>
-static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStream_t st, Staged& out) {
-    constexpr int NW = Src::NW;
-    constexpr int WP = Src::WP;
-    using Cfg = L2Cfg<Src, MODE>;
-    constexpr uint32_t CAP = Cfg::CAP;
-    const int sms = device_sm_count();
-
-    out.err = Scratch(4, st);
-    check_cuda(cudaMemsetAsync(out.err.p, 0, 4, st), "memset err");
-    // R indexes the record space; Reff records exist (fewer for a symmetric product)
-    uint32_t sym_na = 0;
-    uint64_t Reff = R;
-    if constexpr (IsProd<Src>::value) {
-        if (src.sym) {
-            sym_na = src.na;
-            Reff = (uint64_t)src.na * (src.na + 1) / 2;
-        }
-    }
-    Scratch recA((size_t)Reff * 4, st), recB((size_t)Reff * 4, st), subid((size_t)R * 2, st);
-    Scratch bflags_s, cnt_s;
-    uint32_t nbk = 1;
-    const uint64_t C1 = (uint64_t)CAP * 16;
-
-    if (Reff <= C1) {
-        StageScope ss(ST_SCATTER, st);
-        out.boff = Scratch(16, st);
-        bflags_s = Scratch(1, st);
-        if (sym_na)
-            k_iota_tri<<<(unsigned)((Reff + 255) / 256), 256, 0, st>>>(recA.as<uint32_t>(), (uint32_t)Reff, sym_na,
-                                                                     out.boff.as<uint64_t>(), bflags_s.as<uint8_t>());
-        else
-            k_iota<<<(R + 255) / 256, 256, 0, st>>>(recA.as<uint32_t>(), R, out.boff.as<uint64_t>(),
-                                                    bflags_s.as<uint8_t>());
-        note_launch(ST_SCATTER);
-        check_cuda(cudaGetLastError(), "k_iota");
-    } else {
-        const uint32_t bmax = (uint32_t)(max_coarse_splitters<NW>() / 2 + 1);
-        const uint32_t B1 = (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>(bmax, (Reff + C1 - 1) / C1));
-        const uint32_t S = (uint32_t)std::min<uint64_t>(Reff, (uint64_t)B1 * 32);
-        Scratch samp((size_t)S * NW * 8, st);
-        const uint32_t nsp = 2 * (B1 - 1);
-        nbk = nsp + 1;
-        Scratch spl((size_t)nsp * NW * 8, st), pref((size_t)S * 4, st);
-        bflags_s = Scratch(nbk, st);
-        {
-            StageScope ss(ST_SAMPLE, st);
-            k_sample<Src><<<(S + 255) / 256, 256, 0, st>>>(src, R, S, g_sample_seed, samp.as<uint64_t>());
-            note_launch(ST_SAMPLE);
-            check_cuda(cudaGetLastError(), "k_sample");
-            Scratch dk, dc, du;
-            sorted_sample<NW>(samp.as<uint64_t>(), S, st, dk, dc, du, out.err.as<int32_t>());
-            k_select<NW><<<1, 1024, 0, st>>>(dk.as<uint64_t>(), dc.as<double2>(), du.as<uint64_t>(), S, B1,
-                                             pref.as<uint32_t>(), spl.as<uint64_t>(), bflags_s.as<uint8_t>());
-            note_launch(ST_SAMPLE);
-            check_cuda(cudaGetLastError(), "k_select");
-        }
-        cnt_s = Scratch((size_t)nbk * 4, st);
-        check_cuda(cudaMemsetAsync(cnt_s.p, 0, (size_t)nbk * 4, st), "memset");
-        {
-        StageScope ssc(ST_COUNT, st);
-        if constexpr (IsProd<Src>::value) {
-            const size_t sm = (size_t)nsp * NW * 8 + (size_t)kCountCols * NW * 8 + (size_t)nbk * 4;
-            auto kern = k_count_prod<WP, MODE>;
-            smem_attr(kern, sm);
-            const uint64_t tiles = (uint64_t)((src.na + kCountThreads - 1) / kCountThreads) *
-                                   ((nb_terms + kCountCols - 1) / kCountCols);
-            const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)sms * 4));
-            kern<<<grid, kCountThreads, sm, st>>>(src, nb_terms, spl.as<uint64_t>(), nsp, subid.as<uint16_t>(),
-                                                 cnt_s.as<uint32_t>());
-        } else {
-            const size_t sm = (size_t)nsp * NW * 8 + (size_t)nbk * 4;
-            auto kern = k_count_lin<Src>;
-            smem_attr(kern, sm);
-            const unsigned grid = (unsigned)std::max<uint64_t>(
-                1, std::min<uint64_t>(((uint64_t)R + kCountThreads - 1) / kCountThreads, (uint64_t)sms * 4));
-            kern<<<grid, kCountThreads, sm, st>>>(src, R, spl.as<uint64_t>(), nsp, subid.as<uint16_t>(),
-                                                 cnt_s.as<uint32_t>());
-        }
-        note_launch(ST_COUNT);
-        check_cuda(cudaGetLastError(), "k_count");
-        }
-        StageScope ssx(ST_SCATTER, st);
-        out.boff = Scratch((size_t)(nbk + 1) * 8, st);
-        k_scan_counts<<<1, 1024, 0, st>>>(cnt_s.as<uint32_t>(), nbk, out.boff.as<uint64_t>());
-        note_launch(ST_SCATTER);
-        Scratch cursor((size_t)nbk * 8, st);
-        check_cuda(cudaMemcpyAsync(cursor.p, out.boff.p, (size_t)nbk * 8, cudaMemcpyDeviceToDevice, st), "cursor");
-        const size_t sm = (size_t)((nbk + 1) & ~1u) * 4 + (size_t)nbk * 8;
-        smem_attr(k_scatter, sm);
-        const unsigned grid = (unsigned)std::max<uint64_t>(
-            1, std::min<uint64_t>(((uint64_t)R + kScatterChunk - 1) / kScatterChunk, (uint64_t)sms * 2));
-        k_scatter<<<grid, kScatterThreads, sm, st>>>(subid.as<uint16_t>(), R, nbk, cursor.as<uint64_t>(),
-                                                    recA.as<uint32_t>(), sym_na);
-        note_launch(ST_SCATTER);
-        check_cuda(cudaGetLastError(), "k_scatter");
-    }
-
-    // level 2
-    out.nbk = nbk;
-    out.Tkeys = Scratch((size_t)Reff * NW * 8, st);
-    out.Tcoef = Scratch((size_t)Reff * 16, st);
-    Scratch ucount((size_t)nbk * 8, st), ticket(4, st);
-    check_cuda(cudaMemsetAsync(ticket.p, 0, 4, st), "memset");
-    const unsigned grid2 = (unsigned)std::max<uint32_t>(1, std::min<uint32_t>(nbk, (uint32_t)sms * 2));
-    Scratch stacks((size_t)grid2 * kStackCap * sizeof(StackEnt), st);
-    Scratch splscr((size_t)grid2 * (CAP / 2) * NW * 8, st);
-    auto k2 = k_level2<Src, MODE>;
-    smem_attr(k2, Cfg::SMEM);
-    StageScope ss2(ST_LEVEL2, st);
-    note_launch(ST_LEVEL2);
-    note_launch(ST_LEVEL2);  // k_level2 and the scan below
-    k2<<<grid2, kL2Threads, Cfg::SMEM, st>>>(src, nbk, out.boff.as<uint64_t>(), bflags_s.as<uint8_t>(),
-                                            recA.as<uint32_t>(), recB.as<uint32_t>(), subid.as<uint16_t>(),
-                                            ticket.as<uint32_t>(), stacks.as<StackEnt>(), splscr.as<uint64_t>(),
-                                            out.Tkeys.as<uint64_t>(), out.Tcoef.as<double2>(),
-                                            ucount.as<uint64_t>(), out.err.as<int32_t>());
-    check_cuda(cudaGetLastError(), "k_level2");
-    out.uoff = Scratch((size_t)(nbk + 1) * 8, st);
-    k_scan_u64<<<1, 1024, 0, st>>>(ucount.as<uint64_t>(), nbk, out.uoff.as<uint64_t>());
-    check_cuda(cudaGetLastError(), "k_scan_u64");
-}
-
-// Runs the pipeline and builds the output sum (one host synchronisation).
-template <class Src, int MODE>
-static paulib_sum* finish(const Src& src, uint32_t R, uint32_t nb_terms, int32_t n_qubits, cudaStream_t st) {
-    constexpr int WP = Src::WP;
-    Staged sg;
-    run_pipeline<Src, MODE>(src, R, nb_terms, st, sg);
-    struct { uint64_t u; int32_t e; } h{};
-    check_cuda(cudaMemcpyAsync(&h.u, sg.uoff.as<uint64_t>() + sg.nbk, 8, cudaMemcpyDeviceToHost, st), "U copy");
-    check_cuda(cudaMemcpyAsync(&h.e, sg.err.p, 4, cudaMemcpyDeviceToHost, st), "err copy");
-    check_cuda(cudaStreamSynchronize(st), "canonical sync");
-    if (h.e) fail(PAULIB_ERR_INTERNAL, "canonicalisation failed on device (error word " + std::to_string(h.e) + ")");
-    paulib_sum* out = sum_alloc(n_qubits, (int64_t)h.u, false, st);
-    out->is_canonical = 1;
-    if (h.u > 0) {
-        StageScope ss(ST_COMPACT, st);
-        note_launch(ST_COMPACT);
-        const unsigned grid = std::max<uint32_t>(1, std::min<uint32_t>(sg.nbk, (uint32_t)device_sm_count() * 8));
-        k_compact<WP><<<grid, 256, 0, st>>>(sg.nbk, sg.boff.as<uint64_t>(), sg.uoff.as<uint64_t>(),
-                                           sg.Tkeys.as<uint64_t>(), sg.Tcoef.as<double2>(), out->keys, out->coef,
-                                           out->pbase);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) {
-            sum_free(out, st);
-            check_cuda(e, "k_compact");
-        }
-    }
-    return out;
-}
-
-static paulib_sum* empty_canonical(int32_t n_qubits, cudaStream_t st) {
-    paulib_sum* out = sum_alloc(n_qubits, 0, false, st);
-    out->is_canonical = 1;
-    return out;
-}
-
-template <int WP, int MODE>
-static paulib_sum* product_mode(const paulib_sum* a, const paulib_sum* b, cudaStream_t st) {
-    using Src = ProdSrc<WP, MODE>;
-    using V = typename Src::V;
-    const uint32_t R = (uint32_t)(a->n_terms * b->n_terms);
-    Scratch fa, fb;
-    const V* ac;
-    const V* bc;
-    if constexpr (MODE == M_FP64) {
-        ac = reinterpret_cast<const V*>(a->coef);
-        bc = reinterpret_cast<const V*>(b->coef);
-    } else {
-        fa = Scratch((size_t)a->n_terms * 8, st);
-        fb = Scratch((size_t)b->n_terms * 8, st);
-        StageScope ss(ST_CONVERT, st);
-        k_to_f32<MODE><<<(unsigned)((a->n_terms + 255) / 256), 256, 0, st>>>(a->coef, fa.as<float2>(), a->n_terms);
-        k_to_f32<MODE><<<(unsigned)((b->n_terms + 255) / 256), 256, 0, st>>>(b->coef, fb.as<float2>(), b->n_terms);
-        note_launch(ST_CONVERT);
-        note_launch(ST_CONVERT);
-        check_cuda(cudaGetLastError(), "k_to_f32");
-        ac = fa.as<V>();
-        bc = fb.as<V>();
-    }
-    // the same sum on both sides: only i <= j pairs are generated
-    Src src{a->keys, b->keys, a->pbase, b->pbase, ac, bc, (uint32_t)a->n_terms, a == b ? 1u : 0u};
-    return finish<Src, MODE>(src, R, (uint32_t)b->n_terms, a->n_qubits, st);
-}
-
-template <int WP, int MODE>
-static paulib_sum* terms_mode(const paulib_sum* in, cudaStream_t st) {
-    using Src = TermSrc<WP, MODE>;
-    using V = typename Src::V;
-    Scratch f;
-    const V* c;
-    if constexpr (MODE == M_FP64) {
-        c = reinterpret_cast<const V*>(in->coef);
-    } else {
-        f = Scratch((size_t)in->n_terms * 8, st);
-        StageScope ss(ST_CONVERT, st);
-        k_to_f32<MODE><<<(unsigned)((in->n_terms + 255) / 256), 256, 0, st>>>(in->coef, f.as<float2>(), in->n_terms);
-        note_launch(ST_CONVERT);
-        check_cuda(cudaGetLastError(), "k_to_f32");
-        c = f.as<V>();
-    }
-    Src src{in->keys, in->phase, c};
-    return finish<Src, MODE>(src, (uint32_t)in->n_terms, 0, in->n_qubits, st);
-}
 
 paulib_sum* canon_product(const paulib_sum* a, const paulib_sum* b, int mode, cudaStream_t st) {
     const int64_t R = a->n_terms * b->n_terms;
@@ -1297,373 +19,6 @@ paulib_sum* canon_product(const paulib_sum* a, const paulib_sum* b, int mode, cu
     PAULIB_DISPATCH_WP(a->WP, L);
 #undef L
     return nullptr;
-}
-
-paulib_sum* canon_terms(const paulib_sum* in, int mode, cudaStream_t st) {
-    if (in->n_terms == 0) return empty_canonical(in->n_qubits, st);
-    if (in->n_terms >= ((int64_t)1 << 32) - 1) fail(PAULIB_ERR_UNSUPPORTED, "compress needs < 2^32 terms");
-#define L(WP)                                                    \
-    {                                                            \
-        if (mode == M_FP64) return terms_mode<WP, M_FP64>(in, st); \
-        if (mode == M_F32_D64) return terms_mode<WP, M_F32_D64>(in, st); \
-        return terms_mode<WP, M_F32_TWOSUM>(in, st);             \
-    }
-    PAULIB_DISPATCH_WP(in->WP, L);
-#undef L
-    return nullptr;
-}
-
-// ---------------------------------------------------------------- batched products
-//
-// Many independent products canonicalised together.  Problem b's records are
-// the global record range [r0s[b], r0s[b+1]); its products' keys are prefixed
-// by two words (b, 0), so the pipeline's single sort keeps problems apart and
-// emits them in order.  The output of problem b is then copied into its own
-// sum (capacity |A_b||B_b|).
-
-struct ProbDesc {
-    const uint64_t* ak;
-    const uint64_t* bk;
-    const uint8_t* ap;
-    const uint8_t* bp;
-    const void* ac;
-    const void* bc;
-    uint32_t na, nb;
-    uint64_t pad;
-};
-static_assert(sizeof(ProbDesc) == 64, "descriptor is one 64-byte record");
-
-struct OutDesc {
-    uint64_t* keys;
-    double2* coef;
-    uint8_t* pbase;
-    uint64_t pad;
-};
-
-template <int WP_, int MODE>
-struct BatchSrc {
-    static constexpr int WP = WP_;
-    static constexpr int NW = 2 * WP + 2;
-    using V = typename ValT<MODE>::T;
-    const ProbDesc* probs;
-    const uint32_t* r0s;
-    uint32_t nprob;
-    // problem of record r: the largest b with r0s[b] <= r (empty problems are skipped)
-    __device__ __forceinline__ uint32_t find(uint32_t r) const {
-        uint32_t lo = 0, hi = nprob;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (__ldg(r0s + mid) <= r) lo = mid; else hi = mid;
-        }
-        return lo;
-    }
-    __device__ __forceinline__ uint32_t kp(uint32_t r, uint64_t (&k)[NW], bool want_phase) const {
-        const uint32_t b = find(r);
-        const ProbDesc d = probs[b];
-        const uint32_t q = r - __ldg(r0s + b);
-        const uint32_t j = q / d.na, i = q - j * d.na;
-        uint64_t a[2 * WP], bb[2 * WP], o[2 * WP];
-        key_load_g<2 * WP>(d.ak, i, a);
-        key_load_g<2 * WP>(d.bk, j, bb);
-        uint32_t ph = 0;
-        if (want_phase) {
-            ph = string_product<WP>(a, bb, __ldg(d.ap + i), __ldg(d.bp + j), o);
-        } else {
-#pragma unroll
-            for (int w = 0; w < 2 * WP; ++w) o[w] = a[w] ^ bb[w];
-        }
-        k[0] = b;
-        k[1] = 0;
-#pragma unroll
-        for (int w = 0; w < 2 * WP; ++w) k[2 + w] = o[w];
-        return ph;
-    }
-    __device__ __forceinline__ void key(uint32_t r, uint64_t (&k)[NW]) const { kp(r, k, false); }
-    __device__ __forceinline__ uint32_t keyphase(uint32_t r, uint64_t (&k)[NW]) const { return kp(r, k, true); }
-    __device__ __forceinline__ V coefv(uint32_t r, uint32_t ph) const {
-        const uint32_t b = find(r);
-        const ProbDesc d = probs[b];
-        const uint32_t q = r - __ldg(r0s + b);
-        const uint32_t j = q / d.na, i = q - j * d.na;
-        return rot_v(mul_v(static_cast<const V*>(d.ac)[i], static_cast<const V*>(d.bc)[j]), ph);
-    }
-    __device__ __forceinline__ V value(uint32_t r, uint64_t (&k)[NW]) const { return coefv(r, keyphase(r, k)); }
-};
-
-// Distinct output strings per problem.  Within a coarse range the merged
-// terms are in key order, so problems form runs; each thread adds its runs.
-template <int NW>
-__global__ void __launch_bounds__(256) k_batch_counts(uint32_t nbk, const uint64_t* __restrict__ boff,
-                                                      const uint64_t* __restrict__ uoff,
-                                                      const uint64_t* __restrict__ Tkeys,
-                                                      unsigned long long* counts) {
-    for (uint32_t c = blockIdx.x; c < nbk; c += gridDim.x) {
-        const uint64_t src0 = boff[c];
-        const uint64_t cnt = uoff[c + 1] - uoff[c];
-        const uint64_t per = (cnt + blockDim.x - 1) / blockDim.x;
-        const uint64_t t0 = (uint64_t)threadIdx.x * per;
-        const uint64_t t1 = mn<uint64_t>(cnt, t0 + per);
-        uint64_t run = 0, cur = ~0ull;
-        for (uint64_t t = t0; t < t1; ++t) {
-            const uint64_t b = Tkeys[(src0 + t) * NW];
-            if (b != cur) {
-                if (run) atomicAdd(&counts[cur], (unsigned long long)run);
-                cur = b;
-                run = 0;
-            }
-            ++run;
-        }
-        if (run) atomicAdd(&counts[cur], (unsigned long long)run);
-    }
-}
-
-template <int WP>
-__global__ void __launch_bounds__(256) k_batch_scatter(uint32_t nbk, const uint64_t* __restrict__ boff,
-                                                       const uint64_t* __restrict__ uoff,
-                                                       const uint64_t* __restrict__ Tkeys,
-                                                       const double2* __restrict__ Tcoef,
-                                                       const uint64_t* __restrict__ pstart,
-                                                       const OutDesc* __restrict__ outs) {
-    constexpr int NW = 2 * WP + 2;
-    for (uint32_t c = blockIdx.x; c < nbk; c += gridDim.x) {
-        const uint64_t src0 = boff[c];
-        const uint64_t dst0 = uoff[c];
-        const uint64_t cnt = uoff[c + 1] - dst0;
-        for (uint64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
-            uint64_t k[NW];
-            key_load_g<NW>(Tkeys, src0 + t, k);
-            const uint32_t b = (uint32_t)k[0];
-            const uint64_t pos = dst0 + t - pstart[b];
-            const OutDesc o = outs[b];
-            uint64_t kk[2 * WP];
-#pragma unroll
-            for (int w = 0; w < 2 * WP; ++w) kk[w] = k[2 + w];
-            key_store<2 * WP>(o.keys, pos, kk);
-            o.coef[pos] = Tcoef[src0 + t];
-            o.pbase[pos] = (uint8_t)normal_phase<WP>(kk, 0u);
-        }
-    }
-}
-
-// FP32 copies of operand coefficients: job j converts n[j] values.
-struct F32Job {
-    const double2* src;
-    float2* dst;
-    uint64_t n;
-    uint64_t pad;
-};
-__global__ void k_batch_to_f32(const F32Job* jobs, uint32_t njobs) {
-    for (uint32_t j = blockIdx.x; j < njobs; j += gridDim.x) {
-        const F32Job jb = jobs[j];
-        for (uint64_t t = threadIdx.x; t < jb.n; t += blockDim.x)
-            jb.dst[t] = make_float2(__double2float_rn(jb.src[t].x), __double2float_rn(jb.src[t].y));
-    }
-}
-
-}  // namespace paulib
-
-struct paulib_batch_plan {
-    int32_t batch = 0, n_qubits = 0, WP = 0, mode = 0;
-    uint64_t R = 0;
-    std::vector<paulib_sum*> outs;
-    void* desc = nullptr;  // descriptors, offsets, counters (one allocation)
-    void* f32 = nullptr;   // FP32 coefficient copies (mixed-precision modes)
-    void* arena = nullptr;
-    size_t arena_bytes = 0;
-    bool released = false;
-    paulib::ProbDesc* d_probs = nullptr;
-    uint32_t* d_r0s = nullptr;
-    paulib::OutDesc* d_outs = nullptr;
-    unsigned long long* d_counts = nullptr;
-    uint64_t* d_pstart = nullptr;
-    int32_t* d_err = nullptr;
-};
-
-namespace paulib {
-
-template <int WP, int MODE>
-static void batch_launch_impl(paulib_batch_plan* p, cudaStream_t st) {
-    using Src = BatchSrc<WP, MODE>;
-    constexpr int NW = Src::NW;
-    check_cuda(cudaMemsetAsync(p->d_counts, 0, (size_t)p->batch * 8, st), "memset counts");
-    check_cuda(cudaMemsetAsync(p->d_err, 0, 4, st), "memset err");
-    if (p->R == 0) return;
-    Src src{p->d_probs, p->d_r0s, (uint32_t)p->batch};
-    Staged sg;
-    run_pipeline<Src, MODE>(src, (uint32_t)p->R, 0, st, sg);
-    StageScope ss(ST_COMPACT, st);
-    const unsigned grid = std::max<uint32_t>(1, std::min<uint32_t>(sg.nbk, (uint32_t)device_sm_count() * 8));
-    k_or_err<<<1, 32, 0, st>>>(sg.err.as<int32_t>(), p->d_err);
-    k_batch_counts<NW><<<grid, 256, 0, st>>>(sg.nbk, sg.boff.as<uint64_t>(), sg.uoff.as<uint64_t>(),
-                                             sg.Tkeys.as<uint64_t>(), p->d_counts);
-    k_scan_u64<<<1, 1024, 0, st>>>(reinterpret_cast<const uint64_t*>(p->d_counts), (uint32_t)p->batch, p->d_pstart);
-    k_batch_scatter<WP><<<grid, 256, 0, st>>>(sg.nbk, sg.boff.as<uint64_t>(), sg.uoff.as<uint64_t>(),
-                                              sg.Tkeys.as<uint64_t>(), sg.Tcoef.as<double2>(), p->d_pstart,
-                                              p->d_outs);
-    for (int q = 0; q < 4; ++q) note_launch(ST_COMPACT);
-    check_cuda(cudaGetLastError(), "batched output");
-}
-
-static void batch_launch(paulib_batch_plan* p, cudaStream_t st) {
-#define L(WPv)                                                                                  \
-    {                                                                                           \
-        if (p->mode == M_FP64) batch_launch_impl<WPv, M_FP64>(p, st);                           \
-        else if (p->mode == M_F32_D64) batch_launch_impl<WPv, M_F32_D64>(p, st);                \
-        else batch_launch_impl<WPv, M_F32_TWOSUM>(p, st);                                       \
-    }
-    PAULIB_DISPATCH_WP(p->WP, L);
-#undef L
-}
-
-struct ArenaRecordGuard {
-    bool on = true;
-    ArenaRecordGuard() { arena_record_begin(); }
-    size_t end() { on = false; return arena_record_end(); }
-    ~ArenaRecordGuard() { if (on) arena_record_end(); }
-};
-struct ArenaReplayGuard {
-    ArenaReplayGuard(void* b, size_t n) { arena_replay_begin(b, n); }
-    ~ArenaReplayGuard() { arena_replay_end(); }
-};
-
-static void plan_free(paulib_batch_plan* p, cudaStream_t st) {
-    if (!p) return;
-    if (!p->released)
-        for (paulib_sum* s : p->outs) sum_free(s, st);
-    dev_free(p->desc, st);
-    dev_free(p->f32, st);
-    dev_free(p->arena, st);
-    delete p;
-}
-
-paulib_batch_plan* batch_plan_create(int32_t batch, const paulib_sum* const* a, const paulib_sum* const* b,
-                                     int mode, cudaStream_t st) {
-    paulib_batch_plan* p = new paulib_batch_plan;
-    try {
-        p->batch = batch;
-        p->n_qubits = a[0]->n_qubits;
-        p->WP = a[0]->WP;
-        p->mode = mode;
-        std::vector<uint32_t> r0s(batch + 1, 0);
-        uint64_t R = 0;
-        for (int32_t q = 0; q < batch; ++q) {
-            r0s[q] = (uint32_t)R;
-            R += (uint64_t)a[q]->n_terms * (uint64_t)b[q]->n_terms;
-            if (R >= ((uint64_t)1 << 32) - 1) fail(PAULIB_ERR_UNSUPPORTED, "batched products need sum |A_b||B_b| < 2^32");
-        }
-        r0s[batch] = (uint32_t)R;
-        p->R = R;
-        p->outs.assign(batch, nullptr);
-        for (int32_t q = 0; q < batch; ++q) {
-            p->outs[q] = sum_alloc(p->n_qubits, a[q]->n_terms * b[q]->n_terms, false, st);
-            p->outs[q]->is_canonical = 1;
-            p->outs[q]->plan_owned = true;
-            p->outs[q]->n_terms = 0;
-        }
-        // descriptor block
-        const size_t szP = (size_t)batch * sizeof(ProbDesc);
-        const size_t szR = ((size_t)(batch + 1) * 4 + 255) / 256 * 256;
-        const size_t szO = (size_t)batch * sizeof(OutDesc);
-        const size_t szC = ((size_t)batch * 8 + 255) / 256 * 256;
-        const size_t szS = ((size_t)(batch + 1) * 8 + 255) / 256 * 256;
-        const size_t total = szP + szR + szO + szC + szS + 256;
-        p->desc = dev_alloc(total, st);
-        char* base = static_cast<char*>(p->desc);
-        p->d_probs = reinterpret_cast<ProbDesc*>(base);
-        p->d_r0s = reinterpret_cast<uint32_t*>(base + szP);
-        p->d_outs = reinterpret_cast<OutDesc*>(base + szP + szR);
-        p->d_counts = reinterpret_cast<unsigned long long*>(base + szP + szR + szO);
-        p->d_pstart = reinterpret_cast<uint64_t*>(base + szP + szR + szO + szC);
-        p->d_err = reinterpret_cast<int32_t*>(base + szP + szR + szO + szC + szS);
-        std::vector<ProbDesc> hp(batch);
-        std::vector<OutDesc> ho(batch);
-        std::vector<F32Job> jobs;
-        size_t f32_total = 0;
-        if (mode != M_FP64)
-            for (int32_t q = 0; q < batch; ++q) f32_total += (size_t)(a[q]->n_terms + b[q]->n_terms);
-        if (f32_total) p->f32 = dev_alloc(f32_total * sizeof(float2), st);
-        float2* f = static_cast<float2*>(p->f32);
-        for (int32_t q = 0; q < batch; ++q) {
-            ProbDesc& d = hp[q];
-            d.ak = a[q]->keys;
-            d.bk = b[q]->keys;
-            d.ap = a[q]->pbase;
-            d.bp = b[q]->pbase;
-            d.na = (uint32_t)a[q]->n_terms;
-            d.nb = (uint32_t)b[q]->n_terms;
-            d.pad = 0;
-            if (mode == M_FP64) {
-                d.ac = a[q]->coef;
-                d.bc = b[q]->coef;
-            } else {
-                d.ac = f;
-                if (a[q]->n_terms) jobs.push_back(F32Job{a[q]->coef, f, (uint64_t)a[q]->n_terms, 0});
-                f += a[q]->n_terms;
-                d.bc = f;
-                if (b[q]->n_terms) jobs.push_back(F32Job{b[q]->coef, f, (uint64_t)b[q]->n_terms, 0});
-                f += b[q]->n_terms;
-            }
-            ho[q] = OutDesc{p->outs[q]->keys, p->outs[q]->coef, p->outs[q]->pbase, 0};
-        }
-        check_cuda(cudaMemcpyAsync(p->d_probs, hp.data(), szP, cudaMemcpyHostToDevice, st), "desc copy");
-        check_cuda(cudaMemcpyAsync(p->d_r0s, r0s.data(), (size_t)(batch + 1) * 4, cudaMemcpyHostToDevice, st), "r0 copy");
-        check_cuda(cudaMemcpyAsync(p->d_outs, ho.data(), szO, cudaMemcpyHostToDevice, st), "out copy");
-        Scratch jobs_d;
-        if (!jobs.empty()) {
-            jobs_d = Scratch(jobs.size() * sizeof(F32Job), st);
-            check_cuda(cudaMemcpyAsync(jobs_d.p, jobs.data(), jobs.size() * sizeof(F32Job), cudaMemcpyHostToDevice, st),
-                       "job copy");
-            k_batch_to_f32<<<std::min<size_t>(jobs.size(), 4096), 256, 0, st>>>(jobs_d.as<F32Job>(), (uint32_t)jobs.size());
-            note_launch(ST_CONVERT);
-            check_cuda(cudaGetLastError(), "k_batch_to_f32");
-        }
-        // one full run that records the workspace it asks for
-        {
-            ArenaRecordGuard rec;
-            batch_launch(p, st);
-            p->arena_bytes = rec.end();
-        }
-        if (p->arena_bytes) p->arena = dev_alloc(p->arena_bytes, st);
-        check_cuda(cudaStreamSynchronize(st), "plan sync");  // host vectors above must outlive their copies
-    } catch (...) {
-        plan_free(p, st);
-        throw;
-    }
-    return p;
-}
-
-void batch_plan_launch(paulib_batch_plan* p, cudaStream_t st) {
-    ArenaReplayGuard g(p->arena, p->arena_bytes);
-    batch_launch(p, st);
-}
-
-void batch_plan_outputs(paulib_batch_plan* p, cudaStream_t st, paulib_sum** out) {
-    std::vector<unsigned long long> cnt(p->batch);
-    int32_t e = 0;
-    check_cuda(cudaMemcpyAsync(cnt.data(), p->d_counts, (size_t)p->batch * 8, cudaMemcpyDeviceToHost, st), "count copy");
-    check_cuda(cudaMemcpyAsync(&e, p->d_err, 4, cudaMemcpyDeviceToHost, st), "err copy");
-    check_cuda(cudaStreamSynchronize(st), "outputs sync");
-    if (e) fail(PAULIB_ERR_INTERNAL, "batched canonicalisation failed on device (error word " + std::to_string(e) + ")");
-    for (int32_t q = 0; q < p->batch; ++q) {
-        p->outs[q]->n_terms = (int64_t)cnt[q];
-        out[q] = p->outs[q];
-    }
-}
-
-void batch_plan_destroy(paulib_batch_plan* p) { plan_free(p, nullptr); }
-
-void canon_batched(int32_t batch, const paulib_sum* const* a, const paulib_sum* const* b, int mode,
-                   cudaStream_t st, paulib_sum** out) {
-    paulib_batch_plan* p = batch_plan_create(batch, a, b, mode, st);
-    try {
-        batch_plan_outputs(p, st, out);
-    } catch (...) {
-        plan_free(p, st);
-        throw;
-    }
-    for (paulib_sum* s : p->outs) s->plan_owned = false;  // ownership passes to the caller
-    p->released = true;
-    plan_free(p, st);
 }
 
 // ---------------------------------------------------------------- allocation-free product
