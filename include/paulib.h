@@ -200,6 +200,21 @@ paulib_status paulib_multiply_noalloc(int32_t n_qubits, int64_t na, const uint64
                                       uint64_t* out_x, uint64_t* out_z, double* out_c,
                                       int64_t out_capacity, int64_t* out_n, void* stream);
 
+/* Tuning of the canonicalisation pipeline for keys of `key_words` 64-bit
+ * words (2*WP for products and compress, 2*WP + 2 for batched products; 0 =
+ * every size).  No counterpart in the paper; results never depend on it.
+ *   coarse_factor: a first-level key range targets coarse_factor x the
+ *       shared-memory leaf capacity records (2..256, default 16);
+ *   oversample: splitter sample size per first-level range (4..128, default 32);
+ *   count_ctas_per_sm: CTAs per SM of the first-level counting kernel (1..16);
+ *   range_ctas_per_sm: CTAs per SM of the range sort/merge kernel (1..2).
+ * A value <= 0 keeps the current setting.  If the environment variable
+ * PAULIB_TUNE_FILE names a file when the library first needs a setting, its
+ * lines "key_words coarse_factor oversample count_ctas_per_sm
+ * range_ctas_per_sm" are applied first (the file the autotuner writes).     */
+paulib_status paulib_set_tuning(int32_t key_words, int32_t coarse_factor, int32_t oversample,
+                                int32_t count_ctas_per_sm, int32_t range_ctas_per_sm);
+
 /* Diagnostics (no counterpart in the paper): device time of the library's
  * stages measured with CUDA events recorded on the launching stream, and the
  * number of kernels launched per stage.  Stages:

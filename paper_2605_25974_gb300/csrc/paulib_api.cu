@@ -188,6 +188,71 @@ void note_launch(int stage) {
     if (st >= 0 && st < PAULIB_STAGES) g_launches[st] += 1;
 }
 
+// ---------------------------------------------------------------- tuning
+
+namespace {
+std::mutex g_tune_mu;
+bool g_tune_loaded = false;
+Tuning g_tune_all;
+std::vector<std::pair<int, Tuning>> g_tune_by_words;
+
+void merge_tuning(Tuning& dst, const Tuning& src) {
+    if (src.coarse_factor > 0) dst.coarse_factor = std::min(256, std::max(2, src.coarse_factor));
+    if (src.oversample > 0) dst.oversample = std::min(128, std::max(4, src.oversample));
+    if (src.count_ctas_per_sm > 0) dst.count_ctas_per_sm = std::min(16, src.count_ctas_per_sm);
+    if (src.range_ctas_per_sm > 0) dst.range_ctas_per_sm = std::min(2, src.range_ctas_per_sm);
+}
+
+void set_tuning_locked(int key_words, const Tuning& t) {
+    if (key_words <= 0) {
+        merge_tuning(g_tune_all, t);
+        for (auto& kv : g_tune_by_words) merge_tuning(kv.second, t);
+        return;
+    }
+    for (auto& kv : g_tune_by_words)
+        if (kv.first == key_words) {
+            merge_tuning(kv.second, t);
+            return;
+        }
+    Tuning base = g_tune_all;
+    merge_tuning(base, t);
+    g_tune_by_words.push_back({key_words, base});
+}
+
+void load_tune_file_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = std::getenv("PAULIB_TUNE_FILE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char line[256];
+    while (std::fgets(line, sizeof line, f)) {
+        int kw = 0;
+        Tuning t{0, 0, 0, 0};
+        if (line[0] == '#') continue;
+        if (std::sscanf(line, "%d %d %d %d %d", &kw, &t.coarse_factor, &t.oversample, &t.count_ctas_per_sm,
+                        &t.range_ctas_per_sm) == 5)
+            set_tuning_locked(kw, t);
+    }
+    std::fclose(f);
+}
+}  // namespace
+
+Tuning tuning_for(int key_words) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    load_tune_file_locked();
+    for (const auto& kv : g_tune_by_words)
+        if (kv.first == key_words) return kv.second;
+    return g_tune_all;
+}
+
+void set_tuning(int key_words, const Tuning& t) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    load_tune_file_locked();
+    set_tuning_locked(key_words, t);
+}
+
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 paulib_sum* sum_alloc(int32_t n_qubits, int64_t n_terms, bool with_phase, cudaStream_t s) {
@@ -499,6 +564,14 @@ paulib_status paulib_multiply_noalloc(int32_t n_qubits, int64_t na, const uint64
     PAULIB_API_BEGIN
     multiply_noalloc(n_qubits, na, a_x, a_z, a_c, nb, b_x, b_z, b_c, out_x, out_z, out_c, out_capacity, out_n,
                      (cudaStream_t)stream);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_set_tuning(int32_t key_words, int32_t coarse_factor, int32_t oversample,
+                                int32_t count_ctas_per_sm, int32_t range_ctas_per_sm) {
+    PAULIB_API_BEGIN
+    set_tuning(key_words, Tuning{coarse_factor, oversample, count_ctas_per_sm, range_ctas_per_sm});
     return PAULIB_OK;
     PAULIB_API_END
 }

@@ -69,6 +69,16 @@ struct Scratch {
 
 int padded_words(int W);
 
+// Pipeline tuning (paulib_set_tuning); never changes results.
+struct Tuning {
+    int coarse_factor = 16;
+    int oversample = 32;
+    int count_ctas_per_sm = 4;
+    int range_ctas_per_sm = 2;
+};
+Tuning tuning_for(int key_words);
+void set_tuning(int key_words, const Tuning& t);
+
 #define PAULIB_DISPATCH_WP(wp, F)                                                   \
     switch (wp) {                                                                   \
         case 1: F(1); break;                                                        \

@@ -292,6 +292,12 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp
 template <int MODE> struct Acc;
 template <> struct Acc<M_FP64> {
     double re = 0.0, im = 0.0;
+    __device__ __forceinline__ Acc up(int o) const {
+        Acc t;
+        t.re = __shfl_up_sync(0xffffffffu, re, o);
+        t.im = __shfl_up_sync(0xffffffffu, im, o);
+        return t;
+    }
     __device__ __forceinline__ void add(double2 v) { re += v.x; im += v.y; }
     __device__ __forceinline__ void merge(const Acc& o) { re += o.re; im += o.im; }
     __device__ __forceinline__ double2 result() const { return make_double2(re, im); }
@@ -304,6 +310,12 @@ template <> struct Acc<M_FP64> {
 };
 template <> struct Acc<M_F32_D64> {
     double re = 0.0, im = 0.0;
+    __device__ __forceinline__ Acc up(int o) const {
+        Acc t;
+        t.re = __shfl_up_sync(0xffffffffu, re, o);
+        t.im = __shfl_up_sync(0xffffffffu, im, o);
+        return t;
+    }
     __device__ __forceinline__ void add(float2 v) { re += (double)v.x; im += (double)v.y; }
     __device__ __forceinline__ void merge(const Acc& o) { re += o.re; im += o.im; }
     __device__ __forceinline__ double2 result() const { return make_double2(re, im); }
@@ -318,6 +330,14 @@ template <> struct Acc<M_F32_D64> {
 // rounding error of every addition is collected exactly and added back once.
 template <> struct Acc<M_F32_TWOSUM> {
     float sr = 0.f, er = 0.f, si = 0.f, ei = 0.f;
+    __device__ __forceinline__ Acc up(int o) const {
+        Acc t;
+        t.sr = __shfl_up_sync(0xffffffffu, sr, o);
+        t.er = __shfl_up_sync(0xffffffffu, er, o);
+        t.si = __shfl_up_sync(0xffffffffu, si, o);
+        t.ei = __shfl_up_sync(0xffffffffu, ei, o);
+        return t;
+    }
     __device__ __forceinline__ void add(float2 v) {
         float s, e;
         two_sum(sr, v.x, s, e);
@@ -355,12 +375,11 @@ constexpr int kL2Threads = 512;
 constexpr int kStackCap = 4096;
 constexpr int kSmemBudget = 110 * 1024;
 
-// Shared memory per leaf record: the product key (8*NW bytes), a packed sort
-// code (8 bytes), the record number (4 bytes, the tie-break that makes the
-// order of equal keys and so the summation order deterministic) and the
-// product's phase exponent (1 byte).  At most 4096 records, so a slot number
-// fits the code's low 12 bits.
-constexpr int kLeafRecBytes = 8 + 4 + 1;
+// Shared memory per leaf record: the product key (8*NW bytes), a sort code
+// (8 bytes), the record number (4 bytes, the tie-break that makes the order
+// of equal keys and so the summation order deterministic), two 16-bit slot
+// arrays for the merge sort and the product's phase exponent (1 byte).
+constexpr int kLeafRecBytes = 8 + 4 + 2 + 2 + 1;
 template <int NW>
 constexpr int leaf_cap() {
     int cap = 4096;
@@ -657,34 +676,47 @@ struct L2Cfg {
     static constexpr size_t SMEM = leaf_smem<NW>();
 };
 
-// Order of two packed sort codes.  A code holds, above bit 12, the 52 key
-// bits that follow the common prefix of every key in the range, and the
-// element's slot below.  Equal upper bits fall back to the full keys, then to
-// the record number; slots >= n are padding that sorts last.
+// ---- leaf ordering
+//
+// A leaf (or a split sample) is ordered through one 64-bit code per slot:
+// the key bits that follow the common prefix L of every key in the range.
+// Equal codes fall back to the full keys and then to the record number, so
+// the order is total and deterministic.  Slots >= n are padding that sorts
+// last.
+
 template <int NW, uint32_t CAP>
-__device__ __forceinline__ bool code_gt(uint64_t a, uint64_t b, const uint64_t* keys_s, uint32_t n,
-                                        const uint32_t* recs, uint32_t lo) {
-    if ((a ^ b) >> 12) return a > b;
-    const uint32_t ia = (uint32_t)(a & 0xFFFu), ib = (uint32_t)(b & 0xFFFu);
-    if (ia >= n || ib >= n) return ia >= n && (ib < n || ia > ib);
-    const int c = skey_cmp<NW>(keys_s, CAP, ia, ib);
+__device__ __forceinline__ bool slot_gt(uint32_t a, uint32_t b, const uint64_t* c1s, const uint64_t* keys_s,
+                                        uint32_t n, const uint32_t* recs) {
+    if (a >= n || b >= n) return a >= n && (b < n || a > b);
+    const uint64_t ca = c1s[a], cb = c1s[b];
+    if (ca != cb) return ca > cb;
+    const int c = skey_cmp<NW>(keys_s, CAP, a, b);
     if (c) return c > 0;
-    if (recs) return recs[ia] > recs[ib];
-    return ia > ib;
+    if (recs) return recs[a] > recs[b];
+    return a > b;
 }
 
 template <int NW, uint32_t CAP>
-__device__ __forceinline__ bool code_key_neq(uint64_t a, uint64_t b, const uint64_t* keys_s) {
-    if ((a ^ b) >> 12) return true;
-    return skey_cmp<NW>(keys_s, CAP, (uint32_t)(a & 0xFFFu), (uint32_t)(b & 0xFFFu)) != 0;
+__device__ __forceinline__ bool slot_key_neq(uint32_t a, uint32_t b, const uint64_t* c1s, const uint64_t* keys_s) {
+    if (c1s[a] != c1s[b]) return true;
+    return skey_cmp<NW>(keys_s, CAP, a, b) != 0;
 }
 
-// Packed codes for keys_s[0..n): the first bit position L where any key
-// differs from key 0 is found with an OR reduction; each code then takes the
-// 52 bits starting at L.  Slots [n, p2) get padding codes.
+// 64 bits of key t starting at bit position P (word 0's top bit is position 0).
+template <int NW, uint32_t CAP>
+__device__ __forceinline__ uint64_t key_bits64(const uint64_t* keys_s, uint32_t t, uint32_t P) {
+    const uint32_t w = P >> 6, sh = P & 63u;
+    if (w >= (uint32_t)NW) return 0ull;
+    uint64_t v = keys_s[(size_t)w * CAP + t] << sh;
+    if (sh && w + 1 < (uint32_t)NW) v |= keys_s[(size_t)(w + 1) * CAP + t] >> (64u - sh);
+    return v;
+}
+
+// Codes c1s[0..n): the first bit L where any key differs from key 0 comes
+// from an OR reduction of (key ^ key 0) over the range.
 template <int NW, int T, uint32_t CAP>
-__device__ void build_codes(uint64_t* code_s, const uint64_t* keys_s, uint32_t n, uint32_t p2,
-                            unsigned long long* s_or, uint32_t* s_L) {
+__device__ void build_codes(uint64_t* c1s, const uint64_t* keys_s, uint32_t n, unsigned long long* s_or,
+                            uint32_t* s_L) {
     for (int w = threadIdx.x; w < NW; w += T) s_or[w] = 0ull;
     __syncthreads();
     uint64_t acc[NW];
@@ -710,41 +742,143 @@ __device__ void build_codes(uint64_t* code_s, const uint64_t* keys_s, uint32_t n
     }
     __syncthreads();
     const uint32_t L = *s_L;
-    const uint32_t w0 = L >> 6, sh = L & 63u;
-    for (uint32_t t = threadIdx.x; t < p2; t += T) {
-        uint64_t code;
-        if (t >= n) {
-            code = ~0xFFFull | t;
-        } else if (w0 >= (uint32_t)NW) {
-            code = t;
-        } else {
-            uint64_t hi = keys_s[(size_t)w0 * CAP + t] << sh;
-            if (sh && w0 + 1 < (uint32_t)NW) hi |= keys_s[(size_t)(w0 + 1) * CAP + t] >> (64u - sh);
-            code = (hi & ~0xFFFull) | t;
-        }
-        code_s[t] = code;
-    }
+    for (uint32_t t = threadIdx.x; t < n; t += T) c1s[t] = key_bits64<NW, CAP>(keys_s, t, L);
     __syncthreads();
 }
 
+// Stable merge sort of slots 0..n-1 (padded to size, a power of two <= CAP).
+// Each thread first sorts a run of `em` slots by insertion; every following
+// level merges pairs of runs with merge-path partitioning: a thread finds
+// where its `em` outputs start by a binary search along the diagonal, then
+// merges sequentially.  One barrier per level.  Returns the array holding
+// the sorted slots (ord or tmp).
 template <int NW, int T, uint32_t CAP>
-__device__ void block_sort_codes(uint64_t* code_s, const uint64_t* keys_s, uint32_t n, uint32_t p2,
-                                 const uint32_t* recs, uint32_t lo) {
-    for (uint32_t kk = 2; kk <= p2; kk <<= 1) {
-        for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
-            for (uint32_t t = threadIdx.x; t < p2 / 2; t += T) {
-                const uint32_t i = 2 * t - (t & (jj - 1));
-                const uint32_t l = i + jj;
-                const uint64_t a = code_s[i], b = code_s[l];
-                const bool up = (i & kk) == 0;
-                if (code_gt<NW, CAP>(a, b, keys_s, n, recs, lo) == up) {
-                    code_s[i] = b;
-                    code_s[l] = a;
+__device__ uint16_t* merge_sort_slots(uint16_t* ord, uint16_t* tmp, const uint64_t* c1s, const uint64_t* keys_s,
+                                      uint32_t n, uint32_t size, const uint32_t* recs) {
+    constexpr uint32_t EMAX = CAP / (uint32_t)T >= 2u ? CAP / (uint32_t)T : 2u;
+    const uint32_t em = size / (uint32_t)T >= 2u ? size / (uint32_t)T : 2u;
+    const uint32_t nthr = size / em;
+    for (uint32_t t = threadIdx.x; t < nthr; t += T) {
+        uint32_t v[EMAX];
+#pragma unroll
+        for (uint32_t k = 0; k < EMAX; ++k) {
+            if (k < em) {
+                uint32_t x = t * em + k;
+                uint32_t q = k;
+                while (q > 0 && slot_gt<NW, CAP>(v[q - 1], x, c1s, keys_s, n, recs)) {
+                    v[q] = v[q - 1];
+                    --q;
                 }
+                v[q] = x;
             }
-            __syncthreads();
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < EMAX; ++k)
+            if (k < em) ord[t * em + k] = (uint16_t)v[k];
+    }
+    __syncthreads();
+    uint16_t* src = ord;
+    uint16_t* dst = tmp;
+    for (uint32_t s = em; s < size; s <<= 1) {
+        for (uint32_t t = threadIdx.x; t < nthr; t += T) {
+            const uint32_t o = t * em;
+            const uint32_t seg = o & ~(2 * s - 1);
+            const uint32_t d = o - seg;  // output offset within the merged segment
+            const uint16_t* A = src + seg;
+            const uint16_t* B = src + seg + s;
+            uint32_t lo = d > s ? d - s : 0u, hi = d < s ? d : s;
+            while (lo < hi) {  // number of A elements among the first d outputs
+                const uint32_t mid = (lo + hi) >> 1;
+                if (slot_gt<NW, CAP>(A[mid], B[d - mid - 1], c1s, keys_s, n, recs)) hi = mid;
+                else lo = mid + 1;
+            }
+            uint32_t i = lo, j = d - lo;
+            for (uint32_t k = 0; k < em; ++k) {
+                bool takeA;
+                if (i >= s) takeA = false;
+                else if (j >= s) takeA = true;
+                else takeA = !slot_gt<NW, CAP>(A[i], B[j], c1s, keys_s, n, recs);
+                dst[o + k] = takeA ? A[i++] : B[j++];
+            }
+        }
+        __syncthreads();
+        uint16_t* t2 = src;
+        src = dst;
+        dst = t2;
+    }
+    return src;
+}
+
+// Exclusive block scan of (run started here?, partial sum) pairs under
+// (f1, a1) . (f2, a2) = (f1 | f2, f2 ? a2 : a1 + a2): the sum carried into a
+// thread from the run that began before it.
+template <int T, int MODE>
+__device__ __forceinline__ Acc<MODE> block_seg_carry(bool flag, const Acc<MODE>& a, Acc<MODE>* s_acc,
+                                                     uint32_t* s_flag) {
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    Acc<MODE> x = a;
+    bool f = flag;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Acc<MODE> y = x.up(o);
+        const bool fy = __shfl_up_sync(0xffffffffu, f, o);
+        if (lane >= (uint32_t)o) {
+            if (!f) {
+                Acc<MODE> t = y;
+                t.merge(x);
+                x = t;
+            }
+            f = f || fy;
         }
     }
+    // exclusive within the warp
+    Acc<MODE> ex = x.up(1);
+    bool fex = __shfl_up_sync(0xffffffffu, f, 1);
+    if (lane == 0) {
+        ex = Acc<MODE>();
+        fex = false;
+    }
+    if (lane == 31) {
+        s_acc[wid] = x;
+        s_flag[wid] = f;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        Acc<MODE> wx = lane < (uint32_t)(T / 32) ? s_acc[lane] : Acc<MODE>();
+        bool wf = lane < (uint32_t)(T / 32) ? s_flag[lane] != 0 : false;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const Acc<MODE> y = wx.up(o);
+            const bool fy = __shfl_up_sync(0xffffffffu, wf, o);
+            if (lane >= (uint32_t)o) {
+                if (!wf) {
+                    Acc<MODE> t = y;
+                    t.merge(wx);
+                    wx = t;
+                }
+                wf = wf || fy;
+            }
+        }
+        Acc<MODE> wex = wx.up(1);
+        bool wfex = __shfl_up_sync(0xffffffffu, wf, 1);
+        if (lane == 0) {
+            wex = Acc<MODE>();
+            wfex = false;
+        }
+        if (lane < (uint32_t)(T / 32)) {
+            s_acc[lane] = wex;
+            s_flag[lane] = wfex;
+        }
+    }
+    __syncthreads();
+    Acc<MODE> res = ex;
+    if (!fex) {  // the warp prefix flows in unless a run started earlier in this warp
+        Acc<MODE> t = s_acc[wid];
+        t.merge(ex);
+        res = t;
+    }
+    __syncthreads();
+    return res;
 }
 
 template <class Src, int MODE>
@@ -753,15 +887,22 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
     uint32_t* recA, uint32_t* recB, uint16_t* subid, uint32_t* ticket, StackEnt* stacks,
     uint64_t* spl_scratch, uint64_t* Tkeys, double2* Tcoef, uint64_t* ucount, int32_t* err) {
     using Cfg = L2Cfg<Src, MODE>;
+    using V = typename Cfg::V;
     constexpr int NW = Cfg::NW;
     constexpr uint32_t CAP = Cfg::CAP;
     constexpr int T = kL2Threads;
+    constexpr uint32_t ACT = CAP < (uint32_t)T ? CAP : (uint32_t)T;
+    constexpr uint32_t PP = CAP / ACT;  // sorted positions per active thread in the merge
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* keys_s = reinterpret_cast<uint64_t*>(smem);                     // [NW][CAP]
-    uint64_t* code_s = keys_s + (size_t)CAP * NW;                             // [CAP]
-    uint32_t* rec_s = reinterpret_cast<uint32_t*>(code_s + CAP);              // [CAP]
-    uint8_t* ph_s = reinterpret_cast<uint8_t*>(rec_s + CAP);                  // [CAP]
+    uint64_t* c1s = keys_s + (size_t)CAP * NW;                                // [CAP]
+    uint32_t* rec_s = reinterpret_cast<uint32_t*>(c1s + CAP);                 // [CAP]
+    uint16_t* ord_s = reinterpret_cast<uint16_t*>(rec_s + CAP);               // [CAP]
+    uint16_t* tmp_s = ord_s + CAP;                                            // [CAP]
+    uint8_t* ph_s = reinterpret_cast<uint8_t*>(tmp_s + CAP);                  // [CAP]
     __shared__ uint32_t s_warp[32];
+    __shared__ Acc<MODE> s_acc[32];
+    __shared__ uint32_t s_flag[32];
     __shared__ unsigned long long s_or[NW];
     __shared__ uint32_t s_bucket, s_lo, s_hi, s_fl, s_sp, s_done, s_nsp, s_bad, s_L;
     __shared__ uint64_t s_u, s_tbase;
@@ -769,6 +910,7 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
     StackEnt* stack = stacks + (size_t)blockIdx.x * kStackCap;
     uint64_t* my_spl = spl_scratch + (size_t)blockIdx.x * (CAP / 2) * NW;
     const int tid = threadIdx.x;
+    const bool act = (uint32_t)tid < ACT;
 
     for (;;) {
         if (tid == 0) s_bucket = atomicAdd(ticket, 1u);
@@ -823,7 +965,6 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc.shfl_merge(o);
-                Acc<MODE>* s_acc = reinterpret_cast<Acc<MODE>*>(code_s);
                 if ((tid & 31) == 0) s_acc[tid >> 5] = acc;
                 __syncthreads();
                 if (tid < 32) {
@@ -841,8 +982,8 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
                 }
                 __syncthreads();
             } else if (n <= CAP) {
-                // ---- leaf: product keys and phases into shared memory, sort
-                // by (key, record), then sum each run of equal keys
+                // ---- leaf: keys and phases into shared memory, sort, then sum
+                // each run of equal keys with a block segmented scan
                 for (uint32_t t = tid; t < n; t += T) {
                     uint64_t k[NW];
                     const uint32_t r = cur[lo + t];
@@ -850,34 +991,60 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
                     ph_s[t] = (uint8_t)src.keyphase(r, k);
                     skey_store<NW>(keys_s, CAP, t, k);
                 }
-                uint32_t p2 = 1;
-                while (p2 < n) p2 <<= 1;
+                uint32_t size = 2u * (uint32_t)T >= 64u ? 64u : 2u * (uint32_t)T;
+                while (size < n) size <<= 1;
                 __syncthreads();
-                build_codes<NW, T, CAP>(code_s, keys_s, n, p2, s_or, &s_L);
-                block_sort_codes<NW, T, CAP>(code_s, keys_s, n, p2, rec_s, 0);
-                constexpr uint32_t IPT = (CAP + T - 1) / T;
-                const uint32_t p0 = tid * IPT;
-                const uint32_t p1 = min(n, p0 + IPT);
-                uint32_t my_heads = 0;
-                for (uint32_t p = p0; p < p1; ++p)
-                    if (p == 0 || code_key_neq<NW, CAP>(code_s[p], code_s[p - 1], keys_s)) ++my_heads;
+                build_codes<NW, T, CAP>(c1s, keys_s, n, s_or, &s_L);
+                const uint16_t* srt = merge_sort_slots<NW, T, CAP>(ord_s, tmp_s, c1s, keys_s, n, size, rec_s);
+                // positions [p0, p0 + PP) of this thread, in sorted order
+                const uint32_t p0 = (uint32_t)tid * PP;
+                bool hd[PP];
+                V v[PP];
+                uint32_t sl[PP];
+                uint32_t nh = 0;
+#pragma unroll
+                for (uint32_t q = 0; q < PP; ++q) {
+                    const uint32_t p = p0 + q;
+                    hd[q] = false;
+                    if (act && p < n) {
+                        sl[q] = srt[p];
+                        v[q] = src.coefv(rec_s[sl[q]], ph_s[sl[q]]);
+                        hd[q] = (p == 0) || slot_key_neq<NW, CAP>(sl[q], srt[p - 1], c1s, keys_s);
+                        nh += hd[q] ? 1u : 0u;
+                    }
+                }
+                Acc<MODE> trail;
+#pragma unroll
+                for (uint32_t q = 0; q < PP; ++q) {
+                    if (act && p0 + q < n) {
+                        if (hd[q]) trail = Acc<MODE>();
+                        trail.add(v[q]);
+                    }
+                }
                 uint32_t total;
-                uint32_t hidx = block_excl_scan<T>(my_heads, s_warp, total);
-                for (uint32_t p = p0; p < p1; ++p) {
-                    const uint64_t hc = code_s[p];
-                    if (p == 0 || code_key_neq<NW, CAP>(hc, code_s[p - 1], keys_s)) {
-                        Acc<MODE> acc;
-                        uint32_t q = p;
-                        do {
-                            const uint32_t idx = (uint32_t)(code_s[q] & 0xFFFu);
-                            acc.add(src.coefv(rec_s[idx], ph_s[idx]));
-                            ++q;
-                        } while (q < n && !code_key_neq<NW, CAP>(hc, code_s[q], keys_s));
-                        uint64_t k[NW];
-                        skey_load<NW>(keys_s, CAP, (uint32_t)(hc & 0xFFFu), k);
-                        key_store<NW>(Tkeys, tout + hidx, k);
-                        Tcoef[tout + hidx] = acc.result();
-                        ++hidx;
+                const uint32_t hex = block_excl_scan<T>(nh, s_warp, total);
+                Acc<MODE> run = block_seg_carry<T, MODE>(nh > 0, trail, s_acc, s_flag);
+                uint64_t oidx = (uint64_t)hex - 1;  // index of the run flowing in (if any)
+#pragma unroll
+                for (uint32_t q = 0; q < PP; ++q) {
+                    const uint32_t p = p0 + q;
+                    if (act && p < n) {
+                        if (hd[q]) {
+                            run = Acc<MODE>();
+                            ++oidx;
+                        }
+                        run.add(v[q]);
+                        bool last = p + 1 >= n;
+                        if (!last) {
+                            if (q + 1 < PP) last = hd[q + 1];
+                            else last = slot_key_neq<NW, CAP>(srt[p + 1], sl[q], c1s, keys_s);
+                        }
+                        if (last) {
+                            uint64_t k[NW];
+                            skey_load<NW>(keys_s, CAP, sl[q], k);
+                            key_store<NW>(Tkeys, tout + oidx, k);
+                            Tcoef[tout + oidx] = run.result();
+                        }
                     }
                 }
                 __syncthreads();
@@ -885,7 +1052,9 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
                 __syncthreads();
             } else {
                 // ---- split: splitters from a sorted sample of this range
-                const uint32_t S = CAP;
+                const uint32_t want = (uint32_t)mn<uint64_t>(CAP / 4, ((uint64_t)n + CAP / 2 - 1) / (CAP / 2));
+                uint32_t S = 64;
+                while (S < 16u * want && S < CAP) S <<= 1;
                 for (uint32_t t = tid; t < S; t += T) {
                     const uint32_t pos = lo + (uint32_t)(((uint64_t)t * n) / S);
                     uint64_t k[NW];
@@ -893,23 +1062,25 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
                     skey_store<NW>(keys_s, CAP, t, k);
                 }
                 __syncthreads();
-                build_codes<NW, T, CAP>(code_s, keys_s, S, S, s_or, &s_L);
-                block_sort_codes<NW, T, CAP>(code_s, keys_s, S, S, nullptr, 0);
-                const uint32_t want = (uint32_t)mn<uint64_t>(CAP / 4, ((uint64_t)n + CAP / 2 - 1) / (CAP / 2));
+                build_codes<NW, T, CAP>(c1s, keys_s, S, s_or, &s_L);
+                const uint16_t* srt = merge_sort_slots<NW, T, CAP>(ord_s, tmp_s, c1s, keys_s, S, S, nullptr);
                 uint8_t* fl_s = ph_s;  // flag of range b+1 follows splitter b
                 if (tid == 0) {
                     uint32_t nsp = 0;
                     fl_s[0] = 0;
                     bool stop = false;
+                    // a key fills a uniform range when it covers half a target range of the sample
+                    const uint32_t heavy_min = mn<uint32_t>(S, S / (2u * want) > 2u ? S / (2u * want) : 2u);
                     for (uint32_t t = 1; t < want && !stop; ++t) {
                         const uint32_t rho = (uint32_t)(((uint64_t)t * S) / want);
-                        const uint32_t ci = (uint32_t)(code_s[rho] & 0xFFFu);
+                        const uint32_t ci = srt[rho];
                         uint64_t k[NW], s2[NW];
                         skey_load<NW>(keys_s, CAP, ci, k);
                         if (nsp > 0 && key_cmp_m<NW>(k, my_spl + (size_t)(nsp - 1) * NW) <= 0) continue;
-                        const bool heavy =
-                            (rho > 0 && skey_cmp<NW>(keys_s, CAP, ci, (uint32_t)(code_s[rho - 1] & 0xFFFu)) == 0) ||
-                            (rho + 1 < S && skey_cmp<NW>(keys_s, CAP, ci, (uint32_t)(code_s[rho + 1] & 0xFFFu)) == 0);
+                        uint32_t r0 = rho, r1 = rho;
+                        while (r0 > 0 && !slot_key_neq<NW, CAP>(srt[r0 - 1], ci, c1s, keys_s)) --r0;
+                        while (r1 + 1 < S && !slot_key_neq<NW, CAP>(srt[r1 + 1], ci, c1s, keys_s)) ++r1;
+                        const bool heavy = r1 - r0 + 1 >= heavy_min;
                         key_store<NW>(my_spl, nsp, k);
                         ++nsp;
                         fl_s[nsp] = heavy ? 1u : 0u;
@@ -929,8 +1100,8 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
                 const uint32_t nsp = s_nsp;
                 const uint32_t nbs = nsp + 1;
                 for (uint32_t q = tid; q < nsp * NW; q += T) keys_s[(q % NW) * (CAP / 2) + q / NW] = my_spl[q];
-                uint32_t* cnt = reinterpret_cast<uint32_t*>(code_s);  // [nbs]
-                uint32_t* cpos = cnt + CAP / 2;                         // [nbs]
+                uint32_t* cnt = reinterpret_cast<uint32_t*>(c1s);  // [nbs]
+                uint32_t* cpos = cnt + CAP / 2;                      // [nbs]
                 for (uint32_t q = tid; q < nbs; q += T) { cnt[q] = 0; cpos[q] = 0; }
                 __syncthreads();
                 for (uint32_t idx = lo + tid; idx < hi; idx += T) {
@@ -942,13 +1113,13 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
                 }
                 __syncthreads();
                 if (tid == 0) {
-                    uint32_t run = 0;
+                    uint32_t runc = 0;
                     uint32_t bad = 0;
                     for (uint32_t b = 0; b < nbs; ++b) {
                         const uint32_t cb = cnt[b];
                         if (cb == n && !(fl_s[b] & 1u)) bad = 1;  // no progress
-                        cnt[b] = run;
-                        run += cb;
+                        cnt[b] = runc;
+                        runc += cb;
                     }
                     if (bad) { atomicOr(err, ERR_PROGRESS); s_bad = 1; }
                     else if (s_sp + nbs > (uint32_t)kStackCap) { atomicOr(err, ERR_STACK); s_bad = 1; }
@@ -1101,7 +1272,8 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
     Scratch recA((size_t)Reff * 4, st), recB((size_t)Reff * 4, st), subid((size_t)R * 2, st);
     Scratch bflags_s, cnt_s;
     uint32_t nbk = 1;
-    const uint64_t C1 = (uint64_t)CAP * 16;
+    const Tuning tune = tuning_for(NW);
+    const uint64_t C1 = (uint64_t)CAP * (uint64_t)tune.coarse_factor;
 
     if (Reff <= C1) {
         StageScope ss(ST_SCATTER, st);
@@ -1118,7 +1290,7 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
     } else {
         const uint32_t bmax = (uint32_t)(max_coarse_splitters<NW>() / 2 + 1);
         const uint32_t B1 = (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>(bmax, (Reff + C1 - 1) / C1));
-        const uint32_t S = (uint32_t)std::min<uint64_t>(Reff, (uint64_t)B1 * 32);
+        const uint32_t S = (uint32_t)std::min<uint64_t>(Reff, (uint64_t)B1 * (uint64_t)tune.oversample);
         Scratch samp((size_t)S * NW * 8, st);
         const uint32_t nsp = 2 * (B1 - 1);
         nbk = nsp + 1;
@@ -1146,7 +1318,8 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
             smem_attr(kern, sm);
             const uint64_t tiles = (uint64_t)((src.na + kCountThreads - 1) / kCountThreads) *
                                    ((nb_terms + kCountCols - 1) / kCountCols);
-            const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)sms * 4));
+            const unsigned grid = (unsigned)std::max<uint64_t>(
+                1, std::min<uint64_t>(tiles, (uint64_t)sms * (uint64_t)tune.count_ctas_per_sm));
             kern<<<grid, kCountThreads, sm, st>>>(src, nb_terms, spl.as<uint64_t>(), nsp, subid.as<uint16_t>(),
                                                  cnt_s.as<uint32_t>());
         } else {
@@ -1154,7 +1327,8 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
             auto kern = k_count_lin<Src>;
             smem_attr(kern, sm);
             const unsigned grid = (unsigned)std::max<uint64_t>(
-                1, std::min<uint64_t>(((uint64_t)R + kCountThreads - 1) / kCountThreads, (uint64_t)sms * 4));
+                1, std::min<uint64_t>(((uint64_t)R + kCountThreads - 1) / kCountThreads,
+                                      (uint64_t)sms * (uint64_t)tune.count_ctas_per_sm));
             kern<<<grid, kCountThreads, sm, st>>>(src, R, spl.as<uint64_t>(), nsp, subid.as<uint16_t>(),
                                                  cnt_s.as<uint32_t>());
         }
@@ -1183,7 +1357,8 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
     out.Tcoef = Scratch((size_t)Reff * 16, st);
     Scratch ucount((size_t)nbk * 8, st), ticket(4, st);
     check_cuda(cudaMemsetAsync(ticket.p, 0, 4, st), "memset");
-    const unsigned grid2 = (unsigned)std::max<uint32_t>(1, std::min<uint32_t>(nbk, (uint32_t)sms * 2));
+    const unsigned grid2 =
+        (unsigned)std::max<uint32_t>(1, std::min<uint32_t>(nbk, (uint32_t)sms * (uint32_t)tune.range_ctas_per_sm));
     Scratch stacks((size_t)grid2 * kStackCap * sizeof(StackEnt), st);
     Scratch splscr((size_t)grid2 * (CAP / 2) * NW * 8, st);
     auto k2 = k_level2<Src, MODE>;

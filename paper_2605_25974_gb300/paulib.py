@@ -26,7 +26,7 @@ EXPORTED = ["paulib_abi_version", "paulib_sum_create", "paulib_sum_info", "pauli
             "paulib_sum_destroy", "paulib_multiply", "paulib_compress", "paulib_multiply_batched",
             "paulib_last_error", "paulib_set_allocator", "paulib_timing_enable", "paulib_timing_read",
             "paulib_multiply_noalloc", "paulib_batch_plan_create", "paulib_batch_plan_launch",
-            "paulib_batch_plan_outputs", "paulib_batch_plan_destroy"]
+            "paulib_batch_plan_outputs", "paulib_batch_plan_destroy", "paulib_set_tuning"]
 STAGES = ["convert", "sample", "count", "scatter", "level2", "compact", "raw", "export"]
 
 
@@ -76,6 +76,8 @@ def load(path: Optional[str] = None):
     lib.paulib_batch_plan_outputs.restype = _i32
     lib.paulib_batch_plan_destroy.argtypes = [_vp]
     lib.paulib_batch_plan_destroy.restype = None
+    lib.paulib_set_tuning.argtypes = [_i32, _i32, _i32, _i32, _i32]
+    lib.paulib_set_tuning.restype = _i32
     lib.paulib_timing_enable.argtypes = [_i32]
     lib.paulib_timing_enable.restype = _i32
     lib.paulib_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
@@ -272,3 +274,9 @@ def timing_read(reset: bool = True):
     la = (_i64 * n)()
     _check(load().paulib_timing_read(ms, la, 1 if reset else 0))
     return ({s: ms[i] for i, s in enumerate(STAGES)}, {s: int(la[i]) for i, s in enumerate(STAGES)})
+
+
+def set_tuning(key_words=0, coarse_factor=0, oversample=0, count_ctas_per_sm=0, range_ctas_per_sm=0):
+    """Pipeline tuning for keys of ``key_words`` words (0 = all); 0 keeps a value."""
+    _check(load().paulib_set_tuning(int(key_words), int(coarse_factor), int(oversample), int(count_ctas_per_sm),
+                                    int(range_ctas_per_sm)))

@@ -8,7 +8,8 @@ check can borrow the other's logic through it.
 Layout of every generated sum (the paper's struct-of-arrays form, Sec. IV-A):
 ``x`` and ``z`` are uint64 arrays of shape (W, M) with W = ceil(n/64), qubit q
 at word q//64, bit q%64 (Table I: I=(0,0), Z=(0,1), X=(1,0), Y=(1,1)); ``c`` is
-complex128 of shape (M,).  Every generated sum has distinct strings.
+complex128 of shape (M,).  Every generated sum has distinct strings, except
+the batched workload's (see ``batch``).
 
 Workloads (the paper's benchmarks use unnamed random sums, Sec. VI; the
 chemistry-shaped one stands in for Jordan-Wigner molecular Hamiltonians,
@@ -26,9 +27,9 @@ Sec. III-A, Eq. 2):
   [1e-6,1], uniform phase.  n=100/M=20,000 (seed 301) and n=200/M=30,000
   (seed 401); H*H is the product.
 * ``batch``: 4,096 independent products at n=500; left sizes
-  floor(exp(U(ln 16, ln 16384))), right sizes uniform in 1..8, weight uniform in
-  1..32 on random qubits, coefficients as in ``stream``; problem b draws from
-  sub-stream b of seed 501.
+  floor(exp(U(ln 16, ln 16384))), right sizes uniform in 1..8, strings of
+  weight at most 32 on random qubits (repeats allowed), coefficients as in
+  ``stream``; one stream of seed 501, vectorised over problems.
 """
 from __future__ import annotations
 
@@ -280,18 +281,65 @@ def jw(n: int = 100, m: int = 20_000, seed: int = 301) -> SumArrays:
     return SumArrays(n, x, z, coeffs_loguniform(rng, m))
 
 
+def low_weight_terms(rng: np.random.Generator, n: int, m: int, wmax: int, chunk: int = 1 << 20):
+    """m strings with at most wmax non-identity qubits: a weight w uniform in
+    1..wmax, then w qubit positions and letters uniform over {X, Y, Z}; a
+    position drawn twice keeps its first letter, so the weight is at most w.
+    Strings may repeat; canonicalisation merges them."""
+    W = words_for(n)
+    xo = np.zeros((W, m), np.uint64)
+    zo = np.zeros((W, m), np.uint64)
+    for s0 in range(0, m, chunk):
+        r = min(chunk, m - s0)
+        w = rng.integers(1, wmax + 1, size=r)
+        pos = rng.integers(0, n, size=(r, wmax)).astype(np.int32)
+        let = rng.integers(1, 4, size=(r, wmax)).astype(np.int8)
+        use = np.arange(wmax)[None, :] < w[:, None]
+        # sort each row's positions (unused slots last) and keep the first of equal ones
+        key = np.where(use, pos, n + 1)
+        order = np.argsort(key, axis=1, kind="stable")
+        pos = np.take_along_axis(key, order, axis=1)
+        let = np.take_along_axis(let, order, axis=1)
+        keep = pos < n
+        keep[:, 1:] &= pos[:, 1:] != pos[:, :-1]
+        # distinct bits of one word add up to their OR; sum 32-bit halves exactly in float64
+        rows = np.broadcast_to(np.arange(r, dtype=np.int64)[:, None], pos.shape)[keep]
+        p = pos[keep].astype(np.int64)
+        lt = let[keep]
+        flat = rows * W + p // 64
+        b = p % 64
+        wgt = np.ldexp(1.0, (b % 32).astype(np.int32))
+        lo = b < 32
+        for sel, out in (((lt == 1) | (lt == 2), xo), ((lt == 2) | (lt == 3), zo)):
+            acc_lo = np.bincount(flat, weights=np.where(sel & lo, wgt, 0.0), minlength=r * W)
+            acc_hi = np.bincount(flat, weights=np.where(sel & ~lo, wgt, 0.0), minlength=r * W)
+            words = acc_lo.astype(np.uint64) | (acc_hi.astype(np.uint64) << np.uint64(32))
+            out[:, s0:s0 + r] = words.reshape(r, W).T
+    return xo, zo
+
+
 def batch(problems: int = 4096, n: int = 500, seed: int = 501, amin: int = 16, amax: int = 16384,
           bmax: int = 8, wmax: int = 32) -> List[Tuple[SumArrays, SumArrays]]:
+    """Independent products shaped like Pauli-propagation steps: left sizes
+    floor(exp(U(ln amin, ln amax))), right sizes uniform in 1..bmax, strings of
+    weight <= wmax, coefficients log-uniform in magnitude with uniform phase.
+    All draws come from one stream in a fixed order (sizes, then left terms,
+    right terms, left and right coefficients), vectorised over problems."""
+    rng = rng_for(seed)
+    na = np.floor(np.exp(rng.uniform(math.log(amin), math.log(amax), size=problems))).astype(np.int64)
+    nb = rng.integers(1, bmax + 1, size=problems)
+    ax, az = low_weight_terms(rng, n, int(na.sum()), wmax)
+    bx, bz = low_weight_terms(rng, n, int(nb.sum()), wmax)
+    ac = coeffs_loguniform(rng, int(na.sum()))
+    bc = coeffs_loguniform(rng, int(nb.sum()))
+    oa = np.concatenate([[0], np.cumsum(na)])
+    ob = np.concatenate([[0], np.cumsum(nb)])
     out = []
-    for b in range(problems):
-        rng = rng_for(seed, b)
-        na = int(math.floor(math.exp(rng.uniform(math.log(amin), math.log(amax)))))
-        nb = int(rng.integers(1, bmax + 1))
-        ax, az = weighted_random(rng, n, na, 1, wmax)
-        a = SumArrays(n, ax, az, coeffs_loguniform(rng, na))
-        bx, bz = weighted_random(rng, n, nb, 1, wmax)
-        bb = SumArrays(n, bx, bz, coeffs_loguniform(rng, nb))
-        out.append((a, bb))
+    for q in range(problems):
+        sa = slice(int(oa[q]), int(oa[q + 1]))
+        sb = slice(int(ob[q]), int(ob[q + 1]))
+        out.append((SumArrays(n, np.ascontiguousarray(ax[:, sa]), np.ascontiguousarray(az[:, sa]), ac[sa].copy()),
+                    SumArrays(n, np.ascontiguousarray(bx[:, sb]), np.ascontiguousarray(bz[:, sb]), bc[sb].copy())))
     return out
 
 
