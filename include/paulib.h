@@ -193,7 +193,7 @@ paulib_status paulib_set_allocator(paulib_alloc_fn alloc, paulib_free_fn free_, 
 #define PAULIB_NOALLOC_MAX_QUBITS 256
 #define PAULIB_NOALLOC_MAX_TERMS 16384
 #define PAULIB_NOALLOC_MAX_PRODUCTS 65536
-#define PAULIB_NOALLOC_SCRATCH_BYTES 8651008 /* about 8.25 MiB per GPU */
+#define PAULIB_NOALLOC_SCRATCH_BYTES 8995072 /* about 8.6 MiB per GPU */
 paulib_status paulib_multiply_noalloc(int32_t n_qubits, int64_t na, const uint64_t* a_x,
                                       const uint64_t* a_z, const double* a_c, int64_t nb,
                                       const uint64_t* b_x, const uint64_t* b_z, const double* b_c,
@@ -219,14 +219,14 @@ paulib_status paulib_set_tuning(int32_t key_words, int32_t coarse_factor, int32_
  * stages measured with CUDA events recorded on the launching stream, and the
  * number of kernels launched per stage.  Stages:
  *   0 input conversion, 1 splitter sampling and selection, 2 coarse count,
- *   3 coarse scatter, 4 range sort + merge (the per-range worklist kernel),
- *   5 output compaction, 6 raw outer product, 7 export.
+ *   3 coarse scatter, 4 range splitting (the per-range worklist kernel),
+ *   5 output compaction, 6 raw outer product, 7 export, 8 leaf sort + merge.
  * paulib_timing_enable(1) starts recording (0 stops).  paulib_timing_read
  * waits for recorded events, adds their times to ms[PAULIB_STAGES] and the
  * launch counts to launches[PAULIB_STAGES] (either may be NULL), and clears
  * the totals when `reset` is nonzero.  Launch counts are kept even when
  * event timing is off.                                                      */
-#define PAULIB_STAGES 8
+#define PAULIB_STAGES 9
 paulib_status paulib_timing_enable(int32_t on);
 paulib_status paulib_timing_read(double* ms, int64_t* launches, int32_t reset);
 

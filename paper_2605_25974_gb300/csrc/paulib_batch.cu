@@ -81,58 +81,52 @@ struct BatchSrc {
     __device__ __forceinline__ V value(uint32_t r, uint64_t (&k)[NW]) const { return coefv(r, keyphase(r, k)); }
 };
 
-// Distinct output strings per problem.  Within a coarse range the merged
-// terms are in key order, so problems form runs; each thread adds its runs.
+// Distinct output strings per problem.  The merged terms are in key order,
+// so problems form runs; each thread adds up the runs among its slots.
 template <int NW>
-__global__ void __launch_bounds__(256) k_batch_counts(uint32_t nbk, const uint64_t* __restrict__ boff,
-                                                      const uint64_t* __restrict__ uoff,
-                                                      const uint64_t* __restrict__ Tkeys,
-                                                      unsigned long long* counts) {
-    for (uint32_t c = blockIdx.x; c < nbk; c += gridDim.x) {
-        const uint64_t src0 = boff[c];
-        const uint64_t cnt = uoff[c + 1] - uoff[c];
-        const uint64_t per = (cnt + blockDim.x - 1) / blockDim.x;
-        const uint64_t t0 = (uint64_t)threadIdx.x * per;
-        const uint64_t t1 = mn<uint64_t>(cnt, t0 + per);
+__global__ void __launch_bounds__(kChunkThreads) k_batch_counts(uint32_t nch, const uint8_t* __restrict__ oflag,
+                                                              const uint64_t* __restrict__ coff,
+                                                              const uint64_t* __restrict__ Tkeys,
+                                                              unsigned long long* counts) {
+    __shared__ uint32_t s_warp[32];
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
         uint64_t run = 0, cur = ~0ull;
-        for (uint64_t t = t0; t < t1; ++t) {
-            const uint64_t b = Tkeys[(src0 + t) * NW];
+        for_each_flagged(c, oflag, coff, s_warp, [&](uint64_t p, uint64_t) {
+            const uint64_t b = Tkeys[p * NW];
             if (b != cur) {
                 if (run) atomicAdd(&counts[cur], (unsigned long long)run);
                 cur = b;
                 run = 0;
             }
             ++run;
-        }
+        });
         if (run) atomicAdd(&counts[cur], (unsigned long long)run);
     }
 }
 
 template <int WP>
-__global__ void __launch_bounds__(256) k_batch_scatter(uint32_t nbk, const uint64_t* __restrict__ boff,
-                                                       const uint64_t* __restrict__ uoff,
-                                                       const uint64_t* __restrict__ Tkeys,
-                                                       const double2* __restrict__ Tcoef,
-                                                       const uint64_t* __restrict__ pstart,
-                                                       const OutDesc* __restrict__ outs) {
+__global__ void __launch_bounds__(kChunkThreads) k_batch_scatter(uint32_t nch, const uint8_t* __restrict__ oflag,
+                                                               const uint64_t* __restrict__ coff,
+                                                               const uint64_t* __restrict__ Tkeys,
+                                                               const double2* __restrict__ Tcoef,
+                                                               const uint64_t* __restrict__ pstart,
+                                                               const OutDesc* __restrict__ outs) {
     constexpr int NW = 2 * WP + 2;
-    for (uint32_t c = blockIdx.x; c < nbk; c += gridDim.x) {
-        const uint64_t src0 = boff[c];
-        const uint64_t dst0 = uoff[c];
-        const uint64_t cnt = uoff[c + 1] - dst0;
-        for (uint64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+    __shared__ uint32_t s_warp[32];
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        for_each_flagged(c, oflag, coff, s_warp, [&](uint64_t p, uint64_t d) {
             uint64_t k[NW];
-            key_load_g<NW>(Tkeys, src0 + t, k);
+            key_load_g<NW>(Tkeys, p, k);
             const uint32_t b = (uint32_t)k[0];
-            const uint64_t pos = dst0 + t - pstart[b];
+            const uint64_t pos = d - pstart[b];
             const OutDesc o = outs[b];
             uint64_t kk[2 * WP];
 #pragma unroll
             for (int w = 0; w < 2 * WP; ++w) kk[w] = k[2 + w];
             key_store<2 * WP>(o.keys, pos, kk);
-            o.coef[pos] = Tcoef[src0 + t];
+            o.coef[pos] = Tcoef[p];
             o.pbase[pos] = (uint8_t)normal_phase<WP>(kk, 0u);
-        }
+        });
     }
 }
 
@@ -183,14 +177,14 @@ static void batch_launch_impl(paulib_batch_plan* p, cudaStream_t st) {
     Staged sg;
     run_pipeline<Src, MODE>(src, (uint32_t)p->R, 0, st, sg);
     StageScope ss(ST_COMPACT, st);
-    const unsigned grid = std::max<uint32_t>(1, std::min<uint32_t>(sg.nbk, (uint32_t)device_sm_count() * 8));
+    const unsigned grid = std::max<uint32_t>(1, std::min<uint32_t>(sg.nch, (uint32_t)device_sm_count() * 8));
     k_or_err<<<1, 32, 0, st>>>(sg.err.as<int32_t>(), p->d_err);
-    k_batch_counts<NW><<<grid, 256, 0, st>>>(sg.nbk, sg.boff.as<uint64_t>(), sg.uoff.as<uint64_t>(),
-                                             sg.Tkeys.as<uint64_t>(), p->d_counts);
+    k_batch_counts<NW><<<grid, kChunkThreads, 0, st>>>(sg.nch, sg.oflag.as<uint8_t>(), sg.coff.as<uint64_t>(),
+                                                       sg.Tkeys.as<uint64_t>(), p->d_counts);
     k_scan_u64<<<1, 1024, 0, st>>>(reinterpret_cast<const uint64_t*>(p->d_counts), (uint32_t)p->batch, p->d_pstart);
-    k_batch_scatter<WP><<<grid, 256, 0, st>>>(sg.nbk, sg.boff.as<uint64_t>(), sg.uoff.as<uint64_t>(),
-                                              sg.Tkeys.as<uint64_t>(), sg.Tcoef.as<double2>(), p->d_pstart,
-                                              p->d_outs);
+    k_batch_scatter<WP><<<grid, kChunkThreads, 0, st>>>(sg.nch, sg.oflag.as<uint8_t>(), sg.coff.as<uint64_t>(),
+                                                        sg.Tkeys.as<uint64_t>(), sg.Tcoef.as<double2>(), p->d_pstart,
+                                                        p->d_outs);
     for (int q = 0; q < 4; ++q) note_launch(ST_COMPACT);
     check_cuda(cudaGetLastError(), "batched output");
 }

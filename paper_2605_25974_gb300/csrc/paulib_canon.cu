@@ -29,7 +29,8 @@ paulib_sum* canon_product(const paulib_sum* a, const paulib_sum* b, int mode, cu
 // file.  Layout (bytes, each part a multiple of 256): both operands in the
 // packed key form for up to 16384 terms of up to 256 qubits, the record and
 // staging arrays for up to 65536 products, one worklist stack and the
-// splitter scratch of one range CTA, and a few counters.
+// splitter scratch of one range CTA, the output flags and leaf lists, and a
+// few counters.
 
 namespace na {
 constexpr size_t kTerms = PAULIB_NOALLOC_MAX_TERMS;
@@ -49,11 +50,16 @@ constexpr size_t kOffTC = kOffTK + kProducts * kKeyBytes;
 constexpr size_t kOffStack = kOffTC + kProducts * 16;
 constexpr size_t kOffSpl = kOffStack + (size_t)kStackCap * sizeof(StackEnt);
 constexpr size_t kSplBytes = 32768;  // (leaf capacity / 2) splitters of one CTA, largest case
-constexpr size_t kOffMisc = kOffSpl + kSplBytes;
-constexpr size_t kBytes = kOffMisc + 256;
+constexpr size_t kOffFlag = kOffSpl + kSplBytes;
+constexpr size_t kSmallCap = kProducts / 2 + 1;  // warp leaves hold >= 2 records
+constexpr size_t kMedCap = kProducts / 33 + 1;   // block leaves hold more than a warp leaf (>= 32)
+constexpr size_t kOffList = kOffFlag + kProducts;
+constexpr size_t kOffMisc = kOffList + (((kSmallCap + kMedCap) * 8 + 255) & ~(size_t)255);
+constexpr size_t kBytes = kOffMisc + 512;
 static_assert(kBytes == PAULIB_NOALLOC_SCRATCH_BYTES, "scratch size must match the header");
 static_assert(kOffAC % 256 == 0 && kOffAP % 256 == 0 && kOffBK % 256 == 0 && kOffRecA % 256 == 0 &&
-                  kOffSub % 256 == 0 && kOffTK % 256 == 0 && kOffStack % 256 == 0 && kOffMisc % 256 == 0,
+                  kOffSub % 256 == 0 && kOffTK % 256 == 0 && kOffStack % 256 == 0 && kOffFlag % 256 == 0 &&
+                  kOffList % 256 == 0 && kOffMisc % 256 == 0,
               "scratch parts stay 256-byte aligned");
 }  // namespace na
 
@@ -85,20 +91,24 @@ __global__ void k_na_convert(int64_t n, int W, int nq, const uint64_t* __restric
 }
 
 template <int WP>
-__global__ void k_na_output(int W, const uint64_t* __restrict__ ucount, const uint64_t* __restrict__ Tkeys,
-                            const double2* __restrict__ Tcoef, uint64_t* ox, uint64_t* oz, double2* oc,
-                            int64_t cap, int64_t* out_n) {
-    const uint64_t u = *ucount;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < u; t += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t k[2 * WP];
-        key_load_g<2 * WP>(Tkeys, t, k);
-        for (int w = 0; w < W; ++w) {
-            ox[(uint64_t)w * cap + t] = k[w];
-            oz[(uint64_t)w * cap + t] = k[WP + w];
-        }
-        oc[t] = Tcoef[t];
+__global__ void __launch_bounds__(kChunkThreads) k_na_output(int W, uint32_t nch, const uint8_t* __restrict__ oflag,
+                                                           const uint64_t* __restrict__ coff,
+                                                           const uint64_t* __restrict__ Tkeys,
+                                                           const double2* __restrict__ Tcoef, uint64_t* ox,
+                                                           uint64_t* oz, double2* oc, int64_t cap, int64_t* out_n) {
+    __shared__ uint32_t s_warp[32];
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        for_each_flagged(c, oflag, coff, s_warp, [&](uint64_t p, uint64_t d) {
+            uint64_t k[2 * WP];
+            key_load_g<2 * WP>(Tkeys, p, k);
+            for (int w = 0; w < W; ++w) {
+                ox[(uint64_t)w * cap + d] = k[w];
+                oz[(uint64_t)w * cap + d] = k[WP + w];
+            }
+            oc[d] = Tcoef[p];
+        });
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *out_n = (int64_t)u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *out_n = (int64_t)coff[nch];
 }
 
 static std::mutex g_na_mu;
@@ -141,30 +151,35 @@ static void noalloc_run(int32_t n_qubits, int64_t na_, const uint64_t* a_x, cons
     double2* tc = reinterpret_cast<double2*>(base + na::kOffTC);
     StackEnt* stack = reinterpret_cast<StackEnt*>(base + na::kOffStack);
     uint64_t* spl = reinterpret_cast<uint64_t*>(base + na::kOffSpl);
+    uint8_t* oflag = base + na::kOffFlag;
+    uint2* lists = reinterpret_cast<uint2*>(base + na::kOffList);
     unsigned char* misc = base + na::kOffMisc;
-    uint64_t* boff = reinterpret_cast<uint64_t*>(misc);       // [2]
-    uint64_t* ucount = reinterpret_cast<uint64_t*>(misc + 16);  // [1]
-    uint32_t* ticket = reinterpret_cast<uint32_t*>(misc + 24);
-    int32_t* err = reinterpret_cast<int32_t*>(misc + 28);
-    uint8_t* bflags = misc + 32;
+    uint64_t* boff = reinterpret_cast<uint64_t*>(misc);         // [2]
+    uint32_t* ctr = reinterpret_cast<uint32_t*>(misc + 16);     // [4]
+    int32_t* err = reinterpret_cast<int32_t*>(misc + 32);
+    uint8_t* bflags = misc + 36;                                 // [1]
+    uint32_t* ccount = reinterpret_cast<uint32_t*>(misc + 64);  // [8]
+    uint64_t* coff = reinterpret_cast<uint64_t*>(misc + 128);   // [9]
+    static_assert(na::kProducts / kChunk <= 8, "chunk counters fit the counter block");
     const int W = (n_qubits + 63) / 64;
     const uint32_t R = (uint32_t)(na_ * nb_);
-    // counters that must start at zero
-    check_cuda(cudaMemsetAsync(misc, 0, 256, st), "memset scratch counters");
+    const uint32_t nch = (R + kChunk - 1) / kChunk;
+    // counters and offsets that must start at zero
+    check_cuda(cudaMemsetAsync(misc, 0, 512, st), "memset scratch counters");
     if (R > 0) {
+        check_cuda(cudaMemsetAsync(oflag, 0, (size_t)nch * kChunk, st), "memset flags");
         k_na_convert<WP><<<(unsigned)((na_ + 255) / 256), 256, 0, st>>>(
             na_, W, n_qubits, a_x, a_z, reinterpret_cast<const double2*>(a_c), ak, ac, ap, err);
         k_na_convert<WP><<<(unsigned)((nb_ + 255) / 256), 256, 0, st>>>(
             nb_, W, n_qubits, b_x, b_z, reinterpret_cast<const double2*>(b_c), bk, bc, bp, err);
         k_iota<<<(R + 255) / 256, 256, 0, st>>>(recA, R, boff, bflags);
         Src src{ak, bk, ap, bp, ac, bc, (uint32_t)na_};
-        auto k2 = k_level2<Src, M_FP64>;
-        check_cuda(cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM), "attr");
-        k2<<<1, kL2Threads, Cfg::SMEM, st>>>(src, 1u, boff, bflags, recA, recB, sub, ticket, stack, spl, tk, tc,
-                                            ucount, err);
+        L2Bufs lb{recA, recB, sub, ctr, stack, spl, tk, tc, oflag, lists, lists + na::kSmallCap,
+                  (uint32_t)na::kSmallCap, (uint32_t)na::kMedCap, err};
+        launch_level2<Src, M_FP64>(src, 1u, boff, bflags, lb, 1u, nch, ccount, coff, st);
     }
-    k_na_output<WP><<<std::max<unsigned>(1, (R + 255) / 256), 256, 0, st>>>(
-        W, ucount, tk, tc, out_x, out_z, reinterpret_cast<double2*>(out_c), cap, out_n);
+    k_na_output<WP><<<std::max<unsigned>(1, nch), kChunkThreads, 0, st>>>(
+        W, nch, oflag, coff, tk, tc, out_x, out_z, reinterpret_cast<double2*>(out_c), cap, out_n);
     check_cuda(cudaGetLastError(), "noalloc launch");
     int32_t h = 0;
     check_cuda(cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st), "error word copy");

@@ -94,7 +94,7 @@ int device_sm_count();
 // outermost active scope, so nested pipelines count toward the outer stage.
 enum Stage : int {
     ST_CONVERT = 0, ST_SAMPLE = 1, ST_COUNT = 2, ST_SCATTER = 3, ST_LEVEL2 = 4, ST_COMPACT = 5,
-    ST_RAW = 6, ST_EXPORT = 7
+    ST_RAW = 6, ST_EXPORT = 7, ST_LEAF = 8
 };
 struct StageScope {
     StageScope(int stage, cudaStream_t s);

@@ -37,7 +37,7 @@
 namespace paulib {
 
 enum : int { M_FP64 = 0, M_F32_D64 = 1, M_F32_TWOSUM = 2 };
-enum : int32_t { ERR_NONE = 0, ERR_STACK = 1, ERR_PROGRESS = 2, ERR_ITER = 4 };
+enum : int32_t { ERR_NONE = 0, ERR_STACK = 1, ERR_PROGRESS = 2, ERR_ITER = 4, ERR_LIST = 16 };
 
 template <int MODE> struct ValT { using T = float2; };
 template <> struct ValT<M_FP64> { using T = double2; };
@@ -234,6 +234,15 @@ __device__ __forceinline__ int skey_cmp(const uint64_t* s, uint32_t stride, uint
     }
     return 0;
 }
+// skey_cmp over words w0..NW-1 only (the keys agree on the words before).
+template <int NW>
+__device__ __forceinline__ int skey_cmp_from(const uint64_t* s, uint32_t stride, uint32_t a, uint32_t b, int w0) {
+    for (int w = w0; w < NW; ++w) {
+        const uint64_t u = s[(size_t)w * stride + a], v = s[(size_t)w * stride + b];
+        if (u != v) return u < v ? -1 : 1;
+    }
+    return 0;
+}
 template <int NW>
 __device__ __forceinline__ int skey_cmp_r(const uint64_t (&k)[NW], const uint64_t* s, uint32_t stride, uint32_t b) {
 #pragma unroll
@@ -298,6 +307,12 @@ template <> struct Acc<M_FP64> {
         t.im = __shfl_up_sync(0xffffffffu, im, o);
         return t;
     }
+    __device__ __forceinline__ Acc bcast(int l) const {
+        Acc t;
+        t.re = __shfl_sync(0xffffffffu, re, l);
+        t.im = __shfl_sync(0xffffffffu, im, l);
+        return t;
+    }
     __device__ __forceinline__ void add(double2 v) { re += v.x; im += v.y; }
     __device__ __forceinline__ void merge(const Acc& o) { re += o.re; im += o.im; }
     __device__ __forceinline__ double2 result() const { return make_double2(re, im); }
@@ -314,6 +329,12 @@ template <> struct Acc<M_F32_D64> {
         Acc t;
         t.re = __shfl_up_sync(0xffffffffu, re, o);
         t.im = __shfl_up_sync(0xffffffffu, im, o);
+        return t;
+    }
+    __device__ __forceinline__ Acc bcast(int l) const {
+        Acc t;
+        t.re = __shfl_sync(0xffffffffu, re, l);
+        t.im = __shfl_sync(0xffffffffu, im, l);
         return t;
     }
     __device__ __forceinline__ void add(float2 v) { re += (double)v.x; im += (double)v.y; }
@@ -336,6 +357,14 @@ template <> struct Acc<M_F32_TWOSUM> {
         t.er = __shfl_up_sync(0xffffffffu, er, o);
         t.si = __shfl_up_sync(0xffffffffu, si, o);
         t.ei = __shfl_up_sync(0xffffffffu, ei, o);
+        return t;
+    }
+    __device__ __forceinline__ Acc bcast(int l) const {
+        Acc t;
+        t.sr = __shfl_sync(0xffffffffu, sr, l);
+        t.er = __shfl_sync(0xffffffffu, er, l);
+        t.si = __shfl_sync(0xffffffffu, si, l);
+        t.ei = __shfl_sync(0xffffffffu, ei, l);
         return t;
     }
     __device__ __forceinline__ void add(float2 v) {
@@ -674,6 +703,9 @@ struct L2Cfg {
     static constexpr int NW = Src::NW;
     static constexpr int CAP = leaf_cap<NW>();
     static constexpr size_t SMEM = leaf_smem<NW>();
+    // block leaves: at most MCAP records, sorted by one small CTA
+    static constexpr uint32_t MCAP = CAP < 512 ? (uint32_t)CAP : 512u;
+    static constexpr size_t MSMEM = (size_t)MCAP * (8 * NW + kLeafRecBytes);
 };
 
 // ---- leaf ordering
@@ -881,59 +913,738 @@ __device__ __forceinline__ Acc<MODE> block_seg_carry(bool flag, const Acc<MODE>&
     return res;
 }
 
-template <class Src, int MODE>
-__global__ void __launch_bounds__(kL2Threads) k_level2(
-    Src src, uint32_t nbk, const uint64_t* __restrict__ boff, const uint8_t* __restrict__ bflags,
-    uint32_t* recA, uint32_t* recB, uint16_t* subid, uint32_t* ticket, StackEnt* stacks,
-    uint64_t* spl_scratch, uint64_t* Tkeys, double2* Tcoef, uint64_t* ucount, int32_t* err) {
-    using Cfg = L2Cfg<Src, MODE>;
-    using V = typename Cfg::V;
-    constexpr int NW = Cfg::NW;
-    constexpr uint32_t CAP = Cfg::CAP;
-    constexpr int T = kL2Threads;
-    constexpr uint32_t ACT = CAP < (uint32_t)T ? CAP : (uint32_t)T;
-    constexpr uint32_t PP = CAP / ACT;  // sorted positions per active thread in the merge
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* keys_s = reinterpret_cast<uint64_t*>(smem);                     // [NW][CAP]
-    uint64_t* c1s = keys_s + (size_t)CAP * NW;                                // [CAP]
-    uint32_t* rec_s = reinterpret_cast<uint32_t*>(c1s + CAP);                 // [CAP]
-    uint16_t* ord_s = reinterpret_cast<uint16_t*>(rec_s + CAP);               // [CAP]
-    uint16_t* tmp_s = ord_s + CAP;                                            // [CAP]
-    uint8_t* ph_s = reinterpret_cast<uint8_t*>(tmp_s + CAP);                  // [CAP]
-    __shared__ uint32_t s_warp[32];
-    __shared__ Acc<MODE> s_acc[32];
-    __shared__ uint32_t s_flag[32];
-    __shared__ unsigned long long s_or[NW];
-    __shared__ uint32_t s_bucket, s_lo, s_hi, s_fl, s_sp, s_done, s_nsp, s_bad, s_L;
-    __shared__ uint64_t s_u, s_tbase;
+// Key order of two slots (codes, then full keys); records are ignored.
+template <int NW, uint32_t CAP>
+__device__ __forceinline__ int slot_key_cmp(uint32_t a, uint32_t b, const uint64_t* c1s, const uint64_t* keys_s) {
+    const uint64_t ca = c1s[a], cb = c1s[b];
+    if (ca != cb) return ca < cb ? -1 : 1;
+    return skey_cmp<NW>(keys_s, CAP, a, b);
+}
 
-    StackEnt* stack = stacks + (size_t)blockIdx.x * kStackCap;
-    uint64_t* my_spl = spl_scratch + (size_t)blockIdx.x * (CAP / 2) * NW;
+// Block-wide scratch of the range and leaf kernels.
+template <int MODE, int NW>
+struct BlockShared {
+    uint32_t warp[32];
+    Acc<MODE> acc[32];
+    uint32_t flag[32];
+    unsigned long long orr[NW];
+    uint32_t L;
+};
+
+// Device buffers of level 2.  Merged terms are written at the record
+// position of the range they come from: a range [lo, hi) whose records hold
+// U distinct keys writes its terms, in key order, to slots [lo, lo + U) of
+// Tkeys/Tcoef and sets oflag there.  Ranges are disjoint and ordered by key,
+// so the flagged slots, read in position order, are the canonical sum.
+struct L2Bufs {
+    uint32_t* recA;
+    uint32_t* recB;
+    uint16_t* subid;
+    uint32_t* ctr;  // [0] coarse-range ticket, [1] small leaves, [2] medium leaves
+    StackEnt* stacks;
+    uint64_t* spl;
+    uint64_t* Tkeys;
+    double2* Tcoef;
+    uint8_t* oflag;
+    uint2* small;  // ranges for one warp: {lo, n | uniform << 30 | buffer << 31}
+    uint2* med;    // leaves for one CTA
+    uint32_t small_cap, med_cap;
+    int32_t* err;
+};
+
+// ---- block leaf: one CTA orders a range of at most CAP records in shared
+// memory and sums each run of equal keys with a block segmented scan.
+template <class Src, int MODE, int T, uint32_t CAP>
+__device__ void block_leaf(const Src& src, const uint32_t* cur, uint32_t lo, uint32_t n, unsigned char* smem,
+                           BlockShared<MODE, Src::NW>& sh, uint64_t* Tkeys, double2* Tcoef, uint8_t* oflag) {
+    using V = typename Src::V;
+    constexpr int NW = Src::NW;
+    constexpr uint32_t ACT = CAP < (uint32_t)T ? CAP : (uint32_t)T;
+    constexpr uint32_t PP = CAP / ACT;  // sorted positions per active thread
+    uint64_t* keys_s = reinterpret_cast<uint64_t*>(smem);        // [NW][CAP]
+    uint64_t* c1s = keys_s + (size_t)CAP * NW;                   // [CAP]
+    uint32_t* rec_s = reinterpret_cast<uint32_t*>(c1s + CAP);    // [CAP]
+    uint16_t* ord_s = reinterpret_cast<uint16_t*>(rec_s + CAP);  // [CAP]
+    uint16_t* tmp_s = ord_s + CAP;                               // [CAP]
+    uint8_t* ph_s = reinterpret_cast<uint8_t*>(tmp_s + CAP);     // [CAP]
     const int tid = threadIdx.x;
     const bool act = (uint32_t)tid < ACT;
+    for (uint32_t t = tid; t < n; t += T) {
+        uint64_t k[NW];
+        const uint32_t r = cur[lo + t];
+        rec_s[t] = r;
+        ph_s[t] = (uint8_t)src.keyphase(r, k);
+        skey_store<NW>(keys_s, CAP, t, k);
+    }
+    uint32_t size = 64u;
+    while (size < n) size <<= 1;
+    __syncthreads();
+    build_codes<NW, T, CAP>(c1s, keys_s, n, sh.orr, &sh.L);
+    const uint16_t* srt = merge_sort_slots<NW, T, CAP>(ord_s, tmp_s, c1s, keys_s, n, size, rec_s);
+    const uint32_t p0 = (uint32_t)tid * PP;
+    bool hd[PP];
+    V v[PP];
+    uint32_t sl[PP];
+    uint32_t nh = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < PP; ++q) {
+        const uint32_t p = p0 + q;
+        hd[q] = false;
+        if (act && p < n) {
+            sl[q] = srt[p];
+            v[q] = src.coefv(rec_s[sl[q]], ph_s[sl[q]]);
+            hd[q] = (p == 0) || slot_key_neq<NW, CAP>(sl[q], srt[p - 1], c1s, keys_s);
+            nh += hd[q] ? 1u : 0u;
+        }
+    }
+    Acc<MODE> trail;
+#pragma unroll
+    for (uint32_t q = 0; q < PP; ++q) {
+        if (act && p0 + q < n) {
+            if (hd[q]) trail = Acc<MODE>();
+            trail.add(v[q]);
+        }
+    }
+    uint32_t total;
+    const uint32_t hex = block_excl_scan<T>(nh, sh.warp, total);
+    Acc<MODE> run = block_seg_carry<T, MODE>(nh > 0, trail, sh.acc, sh.flag);
+    uint64_t oidx = (uint64_t)lo + hex - 1;  // slot of the run flowing in (if any)
+#pragma unroll
+    for (uint32_t q = 0; q < PP; ++q) {
+        const uint32_t p = p0 + q;
+        if (act && p < n) {
+            if (hd[q]) {
+                run = Acc<MODE>();
+                ++oidx;
+            }
+            run.add(v[q]);
+            bool last = p + 1 >= n;
+            if (!last) {
+                if (q + 1 < PP) last = hd[q + 1];
+                else last = slot_key_neq<NW, CAP>(srt[p + 1], sl[q], c1s, keys_s);
+            }
+            if (last) {
+                uint64_t k[NW];
+                skey_load<NW>(keys_s, CAP, sl[q], k);
+                key_store<NW>(Tkeys, oidx, k);
+                Tcoef[oidx] = run.result();
+                oflag[oidx] = 1;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// ---- warp leaves
+//
+// A range of at most WL records is ordered and merged by one warp with no
+// block barrier: the warp gathers its keys into a private shared-memory
+// slice, builds 64-bit codes after the range's common prefix, sorts
+// (code, slot) pairs with a register/shuffle bitonic network over WL
+// positions (lane l holds positions e*32 + l), and sums equal-key runs with a
+// segmented warp scan.  Outputs go to the staging slots [lo, lo + U) of the
+// range and are marked in the output-flag array.
+
+// A sort entry: one or two 64-bit codes and the slot it came from.
+struct WE {
+    uint64_t c, c2;
+    uint32_t s;
+};
+
+// K: 1 = one code, 2 = two codes, 3 = two codes then the remaining words.
+template <int K>
+__device__ __forceinline__ WE we_shfl_xor(const WE& v, int m) {
+    WE r;
+    r.c = __shfl_xor_sync(0xffffffffu, v.c, m);
+    r.c2 = K >= 2 ? __shfl_xor_sync(0xffffffffu, v.c2, m) : 0ull;
+    r.s = __shfl_xor_sync(0xffffffffu, v.s, m);
+    return r;
+}
+template <int K>
+__device__ __forceinline__ WE we_shfl(const WE& v, int src) {
+    WE r;
+    r.c = __shfl_sync(0xffffffffu, v.c, src);
+    r.c2 = K >= 2 ? __shfl_sync(0xffffffffu, v.c2, src) : 0ull;
+    r.s = __shfl_sync(0xffffffffu, v.s, src);
+    return r;
+}
+template <int K>
+__device__ __forceinline__ WE we_shfl_up(const WE& v, int d) {
+    WE r;
+    r.c = __shfl_up_sync(0xffffffffu, v.c, d);
+    r.c2 = K >= 2 ? __shfl_up_sync(0xffffffffu, v.c2, d) : 0ull;
+    r.s = __shfl_up_sync(0xffffffffu, v.s, d);
+    return r;
+}
+
+// Order of two sort entries: by the codes, then (K = 3) by the key words
+// from w0 on, then by record number (phase-2 entries: padding last).
+// Phase-1 and direct entries hold a slot in s; padding slots carry all-ones
+// codes and record number 0xffffffff, so they sort after every real entry.
+// Phase-2 entries hold (slot | position << 8) in s, with bit 31 marking
+// padding; they are distinct keys and never tie.
+template <int NW, uint32_t WL, int K, bool PH2>
+__device__ __forceinline__ bool we_gt(const WE& a, const WE& b, const uint64_t* wk, const uint32_t* wr, int w0) {
+    if (a.c != b.c) return a.c > b.c;
+    if constexpr (K >= 2) {
+        if (a.c2 != b.c2) return a.c2 > b.c2;
+    }
+    if constexpr (PH2) {
+        const uint32_t pa = a.s >> 31, pb = b.s >> 31;
+        if constexpr (K == 3) {
+            if (!(pa | pb)) {
+                const int c = skey_cmp_from<NW>(wk, WL, a.s & 0xffu, b.s & 0xffu, w0);
+                if (c) return c > 0;
+            }
+        }
+        return pa > pb;
+    } else {
+        const uint32_t ra = wr[a.s], rb = wr[b.s];
+        if constexpr (K == 3) {
+            if (ra != 0xffffffffu && rb != 0xffffffffu) {
+                const int c = skey_cmp_from<NW>(wk, WL, a.s, b.s, w0);
+                if (c) return c > 0;
+            }
+        }
+        return ra > rb;
+    }
+}
+
+// Compare-exchange of rows e and e | D (positions 32*D apart) in a
+// bitonic stage of block size kk.
+template <int NW, uint32_t WL, uint32_t EPL, uint32_t D, int K, bool PH2>
+__device__ __forceinline__ void rows_cx(WE (&x)[EPL], uint32_t kk, uint32_t lane, const uint64_t* wk,
+                                        const uint32_t* wr, int w0) {
+#pragma unroll
+    for (uint32_t e = 0; e < EPL; ++e) {
+        if ((e & D) == 0 && (e | D) < EPL) {
+            const uint32_t e2 = e | D;
+            const bool up = ((e * 32u + lane) & kk) == 0;
+            if (we_gt<NW, WL, K, PH2>(x[e], x[e2], wk, wr, w0) == up) {
+                const WE t = x[e];
+                x[e] = x[e2];
+                x[e2] = t;
+            }
+        }
+    }
+}
+
+// Bitonic network over 32*EPL positions g = e*32 + lane.  The stage loops
+// stay rolled so that the code stays small.
+template <int NW, uint32_t WL, uint32_t EPL, int K, bool PH2>
+__device__ __forceinline__ void warp_sort(WE (&x)[EPL], uint32_t lane, const uint64_t* wk, const uint32_t* wr,
+                                          int w0) {
+#pragma unroll 1
+    for (uint32_t kk = 2; kk <= 32u * EPL; kk <<= 1) {
+#pragma unroll 1
+        for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
+            if (jj >= 32) {
+                if constexpr (EPL >= 2) {
+                    if (jj == 32) rows_cx<NW, WL, EPL, 1, K, PH2>(x, kk, lane, wk, wr, w0);
+                }
+                if constexpr (EPL >= 4) {
+                    if (jj == 64) rows_cx<NW, WL, EPL, 2, K, PH2>(x, kk, lane, wk, wr, w0);
+                }
+            } else {
+#pragma unroll
+                for (uint32_t e = 0; e < EPL; ++e) {
+                    const uint32_t g = e * 32u + lane;
+                    const WE y = we_shfl_xor<K>(x[e], (int)jj);
+                    const bool keep_min = ((lane & jj) == 0) == ((g & kk) == 0);
+                    if (keep_min == we_gt<NW, WL, K, PH2>(x[e], y, wk, wr, w0)) x[e] = y;
+                }
+            }
+        }
+    }
+}
+
+// Run heads in position order: position g starts a run when its entry's
+// codes (and for K = 3 its key words from w0 on) differ from position g-1's.
+// With VERIFY (phase 1, K = 1 on key hashes), equal hashes are checked
+// against the whole keys; the return value reports a mismatch.
+template <int NW, uint32_t WL, uint32_t EPL, int K, bool VERIFY>
+__device__ __forceinline__ bool warp_heads(const WE (&x)[EPL], bool (&hd)[EPL], uint32_t lane, uint32_t n,
+                                           const uint64_t* wk, int w0) {
+    bool bad = false;
+#pragma unroll
+    for (uint32_t e = 0; e < EPL; ++e) {
+        WE prev = we_shfl_up<K>(x[e], 1);
+        if (e > 0) {
+            const WE last = we_shfl<K>(x[e - 1], 31);
+            if (lane == 0) prev = last;
+        }
+        const uint32_t g = e * 32u + lane;
+        bool h = false;
+        if (g < n) {
+            h = g == 0 || x[e].c != prev.c;
+            if constexpr (K >= 2) h = h || x[e].c2 != prev.c2;
+            if constexpr (K == 3) {
+                if (!h) h = skey_cmp_from<NW>(wk, WL, x[e].s, prev.s, w0) != 0;
+            }
+            if constexpr (VERIFY) {
+                if (!h && skey_cmp_from<NW>(wk, WL, x[e].s, prev.s, w0) != 0) bad = true;
+            }
+        }
+        hd[e] = h;
+    }
+    if constexpr (VERIFY) return __any_sync(0xffffffffu, bad);
+    return false;
+}
+
+// Segmented sums of the sorted entries' values over runs of equal keys.
+// DIRECT writes each run's term to slot lo + (run index); otherwise the run
+// total stays in acc[e] at the run's last position and repl[run index]
+// records (slot | position << 8) of that position.  Returns the run count.
+template <class Src, int MODE, int NW, uint32_t WL, uint32_t EPL, bool DIRECT>
+__device__ __forceinline__ uint32_t warp_run_sums(const Src& src, const WE (&x)[EPL], const bool (&hd)[EPL],
+                                                  Acc<MODE> (&acc)[EPL], uint32_t lane, uint32_t n, uint32_t lo,
+                                                  const uint64_t* wk, const uint32_t* wr, const uint8_t* wp,
+                                                  uint16_t* repl, uint64_t* Tkeys, double2* Tcoef,
+                                                  uint8_t* oflag) {
+    Acc<MODE> carry;
+    uint32_t heads_before = 0;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (uint32_t e = 0; e < EPL; ++e) {
+        const uint32_t g = e * 32u + lane;
+        const bool valid = g < n;
+        Acc<MODE> a;
+        if (valid) a.add(src.coefv(wr[x[e].s], wp[x[e].s]));
+        bool f = hd[e];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const Acc<MODE> y = a.up(o);
+            const bool fy = __shfl_up_sync(0xffffffffu, f, o);
+            if (lane >= (uint32_t)o) {
+                if (!f) {
+                    Acc<MODE> t2 = y;
+                    t2.merge(a);
+                    a = t2;
+                }
+                f = f || fy;
+            }
+        }
+        if (!f) {  // no run starts at or before this lane in the row: the open run flows in
+            Acc<MODE> t2 = carry;
+            t2.merge(a);
+            a = t2;
+        }
+        const uint32_t hb = __ballot_sync(0xffffffffu, hd[e]);
+        const uint32_t oidx = heads_before + __popc(hb & lt_mask) + (hd[e] ? 1u : 0u) - 1u;
+        bool next_head;
+        {
+            const bool nh_same = __shfl_down_sync(0xffffffffu, hd[e], 1);
+            bool nh_next = false;
+            if (e + 1 < EPL) nh_next = __shfl_sync(0xffffffffu, hd[e + 1 < EPL ? e + 1 : e], 0);
+            next_head = lane < 31 ? nh_same : nh_next;
+        }
+        const bool last = valid && (g + 1 >= n || next_head);
+        if (last) {
+            if constexpr (DIRECT) {
+                uint64_t k[NW];
+                skey_load<NW>(wk, WL, x[e].s, k);
+                key_store<NW>(Tkeys, (uint64_t)lo + oidx, k);
+                Tcoef[(uint64_t)lo + oidx] = a.result();
+                oflag[(uint64_t)lo + oidx] = 1;
+            } else {
+                repl[oidx] = (uint16_t)(x[e].s | (g << 8));
+            }
+        }
+        acc[e] = a;
+        carry = a.bcast(31);
+        heads_before += __popc(hb);
+    }
+    return heads_before;
+}
+
+// Phase 2: the U distinct keys, ordered by their codes, written to slots
+// lo .. lo + U - 1 with the run totals held by the phase-1 lanes.
+template <class Src, int MODE, int NW, uint32_t WL, uint32_t EPL, uint32_t EPL2, int K>
+__device__ __forceinline__ void warp_phase2(const Acc<MODE> (&acc)[EPL], uint32_t U, uint32_t lane, uint32_t lo,
+                                            const uint64_t* wk, const uint16_t* repl, uint32_t L, uint32_t L2,
+                                            int w0, uint64_t* Tkeys, double2* Tcoef, uint8_t* oflag) {
+    WE y[EPL2];
+#pragma unroll
+    for (uint32_t e = 0; e < EPL2; ++e) {
+        const uint32_t u = e * 32u + lane;
+        if (u < U) {
+            const uint32_t rv = repl[u];
+            const uint32_t sl = rv & 0xffu;
+            y[e] = WE{key_bits64<NW, WL>(wk, sl, L), K >= 2 ? key_bits64<NW, WL>(wk, sl, L2) : 0ull, rv};
+        } else {
+            y[e] = WE{~0ull, ~0ull, 0x80000000u | u};
+        }
+    }
+    warp_sort<NW, WL, EPL2, K, true>(y, lane, wk, nullptr, w0);
+#pragma unroll
+    for (uint32_t e = 0; e < EPL2; ++e) {
+        const uint32_t u = e * 32u + lane;
+        const uint32_t rv = y[e].s;
+        const uint32_t g = (rv >> 8) & 0xffu;
+        Acc<MODE> v;
+#pragma unroll
+        for (uint32_t r = 0; r < EPL; ++r) {
+            const Acc<MODE> t = acc[r].bcast((int)(g & 31u));
+            if (r == (g >> 5)) v = t;
+        }
+        if (u < U) {
+            uint64_t k[NW];
+            skey_load<NW>(wk, WL, rv & 0xffu, k);
+            key_store<NW>(Tkeys, (uint64_t)lo + u, k);
+            Tcoef[(uint64_t)lo + u] = v.result();
+            oflag[(uint64_t)lo + u] = 1;
+        }
+    }
+}
+
+template <class Src, int MODE, int NW, uint32_t WL, uint32_t EPL2, uint32_t EPL>
+__device__ __forceinline__ void warp_phase2_k(int K, const Acc<MODE> (&acc)[EPL], uint32_t U, uint32_t lane,
+                                              uint32_t lo, const uint64_t* wk, const uint16_t* repl, uint32_t L,
+                                              uint32_t L2, int w0, uint64_t* Tkeys, double2* Tcoef,
+                                              uint8_t* oflag) {
+    if (K == 1) warp_phase2<Src, MODE, NW, WL, EPL, EPL2, 1>(acc, U, lane, lo, wk, repl, L, L2, w0, Tkeys, Tcoef, oflag);
+    else if (K == 2) warp_phase2<Src, MODE, NW, WL, EPL, EPL2, 2>(acc, U, lane, lo, wk, repl, L, L2, w0, Tkeys, Tcoef, oflag);
+    else warp_phase2<Src, MODE, NW, WL, EPL, EPL2, 3>(acc, U, lane, lo, wk, repl, L, L2, w0, Tkeys, Tcoef, oflag);
+}
+
+// First position >= P (word 0's top bit is position 0) where mask m has a
+// set bit, or 64*NW.
+template <int NW>
+__device__ __forceinline__ uint32_t first_set_from(const uint64_t (&m)[NW], uint32_t P) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        if (64u * w + 63u < P) continue;
+        uint64_t mm = m[w];
+        if (P > 64u * w) mm &= ~0ull >> (P - 64u * w);
+        if (mm) return 64u * w + (uint32_t)__clzll((long long)mm);
+    }
+    return 64u * NW;
+}
+
+// 64-bit hash of a key (multiply-xorshift per word); equal keys hash equal.
+template <int NW>
+__device__ __forceinline__ uint64_t key_hash(const uint64_t (&k)[NW]) {
+    uint64_t h = 0x243f6a8885a308d3ull;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        h = (h ^ k[w]) * 0x9e3779b97f4a7c15ull;
+        h ^= h >> 29;
+    }
+    return h;
+}
+
+// One warp leaf of n <= 32*EPL records.  Phase 1 sorts (key hash, record),
+// so that equal keys meet (each meeting is checked against the whole keys),
+// and sums each run; phase 2 orders the distinct keys by codes of their
+// varying bits.  Equal keys are frequent (e.g. both orders of a commuting
+// pair) and would otherwise be compared word by word at every step of the
+// network.  A hash clash between different keys falls back to one sort by
+// the whole key.
+template <class Src, int MODE, int NW, uint32_t WL, uint32_t EPL>
+__device__ void warp_leaf_rows(const Src& src, const uint32_t* cur, uint32_t lo, uint32_t n, unsigned char* wsm,
+                               uint64_t* Tkeys, double2* Tcoef, uint8_t* oflag) {
+    static_assert(EPL * 32 <= WL && WL <= 128, "network fits the slice");
+    uint64_t* wk = reinterpret_cast<uint64_t*>(wsm);                   // [NW][WL]
+    uint32_t* wr = reinterpret_cast<uint32_t*>(wk + (size_t)NW * WL);  // [WL]
+    uint16_t* repl = reinterpret_cast<uint16_t*>(wr + WL);             // [WL]
+    uint8_t* wp = reinterpret_cast<uint8_t*>(repl + WL);               // [WL]
+    const uint32_t lane = threadIdx.x & 31u;
+    uint64_t hh[EPL];
+#pragma unroll
+    for (uint32_t e = 0; e < EPL; ++e) {
+        const uint32_t t = e * 32u + lane;
+        hh[e] = ~0ull;
+        if (t < n) {
+            uint64_t k[NW];
+            const uint32_t r = cur[lo + t];
+            wr[t] = r;
+            wp[t] = (uint8_t)src.keyphase(r, k);
+            skey_store<NW>(wk, WL, t, k);
+            hh[e] = key_hash<NW>(k);
+        } else {
+            wr[t] = 0xffffffffu;
+        }
+    }
+    __syncwarp();
+    // Variation mask: the positions where some key differs from key 0.  The
+    // first code holds the 64 positions from the first varying one, L; the
+    // second the 64 from the first varying position L2 >= L + 64.  Keys agree
+    // everywhere else, up to the first varying position after L2 + 64.
+    uint64_t m[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        uint64_t v = 0;
+#pragma unroll
+        for (uint32_t e = 0; e < EPL; ++e) {
+            const uint32_t t = e * 32u + lane;
+            if (t < n) v |= wk[(size_t)w * WL + t] ^ wk[(size_t)w * WL];
+        }
+        const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(v >> 32));
+        const uint32_t lo32 = __reduce_or_sync(0xffffffffu, (uint32_t)v);
+        m[w] = ((uint64_t)hi << 32) | lo32;
+    }
+    const uint32_t L = first_set_from<NW>(m, 0u);
+    const uint32_t L2 = L + 64u < 64u * NW ? first_set_from<NW>(m, L + 64u) : 64u * NW;
+    const bool more = L2 + 64u < 64u * NW && first_set_from<NW>(m, L2 + 64u) < 64u * NW;
+    const int K = L2 >= 64u * NW ? 1 : (more ? 3 : 2);
+    const int w0 = (int)((L2 + 64u) >> 6);
+    const int wl0 = (int)(L >> 6);  // first word where keys can differ
+    WE x[EPL];
+    bool hd[EPL];
+    Acc<MODE> acc[EPL];
+#pragma unroll
+    for (uint32_t e = 0; e < EPL; ++e) {
+        const uint32_t t = e * 32u + lane;
+        x[e] = WE{hh[e], 0ull, t};
+    }
+    warp_sort<NW, WL, EPL, 1, false>(x, lane, wk, wr, 0);
+    if (!warp_heads<NW, WL, EPL, 1, true>(x, hd, lane, n, wk, wl0)) {
+        const uint32_t U = warp_run_sums<Src, MODE, NW, WL, EPL, false>(src, x, hd, acc, lane, n, lo, wk, wr, wp,
+                                                                         repl, Tkeys, Tcoef, oflag);
+        __syncwarp();
+        if (U <= 32u) {
+            warp_phase2_k<Src, MODE, NW, WL, 1, EPL>(K, acc, U, lane, lo, wk, repl, L, L2, w0, Tkeys, Tcoef, oflag);
+        } else if constexpr (EPL >= 2) {
+            if (U <= 64u) {
+                warp_phase2_k<Src, MODE, NW, WL, 2, EPL>(K, acc, U, lane, lo, wk, repl, L, L2, w0, Tkeys, Tcoef,
+                                                         oflag);
+            } else if constexpr (EPL >= 4) {
+                warp_phase2_k<Src, MODE, NW, WL, 4, EPL>(K, acc, U, lane, lo, wk, repl, L, L2, w0, Tkeys, Tcoef,
+                                                         oflag);
+            }
+        }
+        __syncwarp();
+        return;
+    }
+    // a hash clash: one sort by codes and the whole key, then direct sums
+#pragma unroll
+    for (uint32_t e = 0; e < EPL; ++e) {
+        const uint32_t t = e * 32u + lane;
+        x[e] = t < n ? WE{key_bits64<NW, WL>(wk, t, L), key_bits64<NW, WL>(wk, t, L2), t} : WE{~0ull, ~0ull, t};
+    }
+    warp_sort<NW, WL, EPL, 3, false>(x, lane, wk, wr, w0);
+    warp_heads<NW, WL, EPL, 3, false>(x, hd, lane, n, wk, w0);
+    warp_run_sums<Src, MODE, NW, WL, EPL, true>(src, x, hd, acc, lane, n, lo, wk, wr, wp, repl, Tkeys, Tcoef, oflag);
+    __syncwarp();
+}
+
+// A warp leaf sorts with the smallest network that holds its n records.
+template <class Src, int MODE, int NW, uint32_t WL>
+__device__ __forceinline__ void warp_leaf(const Src& src, const uint32_t* cur, uint32_t lo, uint32_t n,
+                                          unsigned char* wsm, uint64_t* Tkeys, double2* Tcoef, uint8_t* oflag) {
+    if (n <= 32) {
+        warp_leaf_rows<Src, MODE, NW, WL, 1>(src, cur, lo, n, wsm, Tkeys, Tcoef, oflag);
+        return;
+    }
+    if constexpr (WL >= 64) {
+        if (n <= 64) {
+            warp_leaf_rows<Src, MODE, NW, WL, 2>(src, cur, lo, n, wsm, Tkeys, Tcoef, oflag);
+            return;
+        }
+        if constexpr (WL >= 128) warp_leaf_rows<Src, MODE, NW, WL, 4>(src, cur, lo, n, wsm, Tkeys, Tcoef, oflag);
+    }
+}
+
+// A range whose records all share one key, summed by one warp.
+template <class Src, int MODE>
+__device__ void warp_uniform(const Src& src, const uint32_t* cur, uint32_t lo, uint32_t n, uint64_t* Tkeys,
+                             double2* Tcoef, uint8_t* oflag) {
+    constexpr int NW = Src::NW;
+    const uint32_t lane = threadIdx.x & 31u;
+    Acc<MODE> acc;
+    for (uint32_t t = lane; t < n; t += 32u) {
+        uint64_t k[NW];
+        acc.add(src.value(cur[lo + t], k));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc.shfl_merge(o);
+    if (lane == 0) {
+        uint64_t k[NW];
+        src.key(cur[lo], k);
+        key_store<NW>(Tkeys, lo, k);
+        Tcoef[lo] = acc.result();
+        oflag[lo] = 1;
+    }
+}
+
+constexpr int kLeafThreads = 128;   // threads of the block-leaf kernel
+constexpr uint32_t kUniformWarpMax = 4096;  // longest all-equal range summed by one warp
+constexpr int kWarpLeafWarps = 8;   // warps per CTA of the warp-leaf kernel
+
+// Warp-leaf capacity: up to 128 records, with each warp's slice of shared
+// memory (keys, record numbers, phases) kept within 5.5 KB so that many warps
+// stay resident (the leaf is bound by latency, not bandwidth).
+template <int NW>
+constexpr uint32_t warp_leaf_cap() {
+    uint32_t wl = 128;
+    while (wl > 32 && wl * (8u * NW + 7u) > 5632u) wl >>= 1;
+    return wl;
+}
+template <int NW>
+constexpr size_t warp_leaf_bytes() {
+    return ((size_t)warp_leaf_cap<NW>() * (8 * NW + 7) + 15) & ~(size_t)15;
+}
+
+template <class Src, int MODE>
+__global__ void __launch_bounds__(kLeafThreads) k_leaf_block(Src src, L2Bufs b) {
+    using Cfg = L2Cfg<Src, MODE>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ BlockShared<MODE, Cfg::NW> sh;
+    const uint32_t cnt = mn<uint32_t>(b.ctr[2], b.med_cap);
+    for (uint32_t e = blockIdx.x; e < cnt; e += gridDim.x) {
+        const uint2 en = b.med[e];
+        const uint32_t* cur = (en.y >> 31) ? b.recB : b.recA;
+        block_leaf<Src, MODE, kLeafThreads, Cfg::MCAP>(src, cur, en.x, en.y & 0x7fffffffu, smem, sh, b.Tkeys,
+                                                     b.Tcoef, b.oflag);
+    }
+}
+
+template <class Src, int MODE>
+__global__ void __launch_bounds__(kWarpLeafWarps * 32) k_leaf_warp(Src src, L2Bufs b) {
+    constexpr int NW = Src::NW;
+    constexpr uint32_t WL = warp_leaf_cap<NW>();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t w = threadIdx.x >> 5;
+    unsigned char* wsm = smem + (size_t)w * warp_leaf_bytes<NW>();
+    const uint32_t cnt = mn<uint32_t>(b.ctr[1], b.small_cap);
+    const uint32_t nwarp = gridDim.x * kWarpLeafWarps;
+    for (uint32_t e = blockIdx.x * kWarpLeafWarps + w; e < cnt; e += nwarp) {
+        const uint2 en = b.small[e];
+        const uint32_t* cur = (en.y >> 31) ? b.recB : b.recA;
+        const uint32_t n = en.y & 0x3fffffffu;
+        if (en.y & 0x40000000u) warp_uniform<Src, MODE>(src, cur, en.x, n, b.Tkeys, b.Tcoef, b.oflag);
+        else warp_leaf<Src, MODE, NW, WL>(src, cur, en.x, n, wsm, b.Tkeys, b.Tcoef, b.oflag);
+    }
+}
+
+// 64 bits of a register key starting at bit position P (word 0's top bit is
+// position 0); zero beyond the key.
+template <int NW>
+__device__ __forceinline__ uint64_t reg_bits64(const uint64_t (&k)[NW], uint32_t P) {
+    const uint32_t w = P >> 6, sh = P & 63u;
+    uint64_t v = 0, nx = 0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        if ((uint32_t)q == w) v = k[q];
+        if ((uint32_t)q == w + 1) nx = k[q];
+    }
+    return sh ? (v << sh) | (nx >> (64u - sh)) : v;
+}
+
+// Compares bits [0, P) of a register key with those of word-major key 0.
+template <int NW>
+__device__ __forceinline__ int prefix_cmp(const uint64_t (&k)[NW], const uint64_t* s, uint32_t stride, uint32_t P) {
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        if (64u * q >= P) break;
+        uint64_t a = k[q], b = s[(size_t)q * stride];
+        const uint32_t nb = P - 64u * q;
+        if (nb < 64u) {
+            const uint64_t m = ~0ull << (64u - nb);
+            a &= m;
+            b &= m;
+        }
+        if (a != b) return a < b ? -1 : 1;
+    }
+    return 0;
+}
+
+// ---- routing: a range that needs no split at this point goes to the leaf
+// lists (or is emitted at once when it holds one record); a range to split,
+// or one whose keys are all equal, goes on the CTA's stack.  Called by all
+// 32 lanes of a warp; `valid` marks the lanes that hold a range.
+template <class Src, int MODE, uint32_t WL, uint32_t MCAP>
+__device__ __forceinline__ void route_range(const Src& src, const L2Bufs& b, bool valid, uint32_t lo, uint32_t n,
+                                            uint32_t fl, StackEnt* stack, uint32_t* s_sp) {
+    constexpr int NW = Src::NW;
+    const uint32_t lane = threadIdx.x & 31u;
+    int kind = -1;  // 0 one record, 1 warp list, 2 block leaf, 3 stack
+    if (valid && n > 0) {
+        if (n == 1) kind = 0;
+        else if (fl & SF_UNIFORM) kind = n <= kUniformWarpMax ? 1 : 3;
+        else if (n <= WL) kind = 1;
+        else if (n <= MCAP) kind = 2;
+        else kind = 3;
+    }
+    const uint32_t bufbit = ((fl & SF_INB) ? 0x80000000u : 0u) | ((fl & SF_UNIFORM) ? 0x40000000u : 0u);
+    if (kind == 0) {
+        const uint32_t* cur = (fl & SF_INB) ? b.recB : b.recA;
+        uint64_t k[NW];
+        Acc<MODE> a;
+        a.add(src.value(cur[lo], k));
+        key_store<NW>(b.Tkeys, lo, k);
+        b.Tcoef[lo] = a.result();
+        b.oflag[lo] = 1;
+    }
+#pragma unroll
+    for (int list = 1; list <= 2; ++list) {
+        const uint32_t m = __ballot_sync(0xffffffffu, kind == list);
+        if (m) {
+            const uint32_t leader = (uint32_t)__ffs(m) - 1u;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(&b.ctr[list], (uint32_t)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (kind == list) {
+                const uint32_t idx = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
+                const uint32_t cap = list == 1 ? b.small_cap : b.med_cap;
+                uint2* dst = list == 1 ? b.small : b.med;
+                if (idx < cap) dst[idx] = make_uint2(lo, n | bufbit);
+                else atomicOr(b.err, ERR_LIST);
+            }
+        }
+    }
+    if (kind == 3) {
+        const uint32_t p = atomicAdd(s_sp, 1u);
+        if (p < (uint32_t)kStackCap) stack[p] = StackEnt{lo, lo + n, fl, 0u};
+        else atomicOr(b.err, ERR_STACK);
+    }
+}
+
+// ---- level 2: one CTA per coarse range (taken from a ticket counter) splits
+// it until every piece fits a leaf.  Splitters come from a sorted sample of
+// the range's own records; a key that fills a large share of the sample gets
+// a range of its own, which is reduced here without sorting.
+template <class Src, int MODE>
+__global__ void __launch_bounds__(kL2Threads, 2) k_level2(Src src, uint32_t nbk, const uint64_t* __restrict__ boff,
+                                                       const uint8_t* __restrict__ bflags, L2Bufs b,
+                                                       uint32_t child_target) {
+    using Cfg = L2Cfg<Src, MODE>;
+    constexpr int NW = Cfg::NW;
+    constexpr uint32_t CAP = Cfg::CAP;
+    constexpr uint32_t WL = warp_leaf_cap<NW>();
+    constexpr int T = kL2Threads;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* keys_s = reinterpret_cast<uint64_t*>(smem);        // [NW][CAP]
+    uint64_t* c1s = keys_s + (size_t)CAP * NW;                   // [CAP]
+    uint16_t* ord_s = reinterpret_cast<uint16_t*>(c1s + CAP);    // [CAP]
+    uint16_t* tmp_s = ord_s + CAP;                               // [CAP]
+    uint8_t* fl_s = reinterpret_cast<uint8_t*>(tmp_s + CAP);     // [CAP]: flag of range p+1 follows splitter p
+    __shared__ BlockShared<MODE, NW> sh;
+    __shared__ uint32_t s_bucket, s_lo, s_hi, s_fl, s_sp, s_done, s_bad;
+
+    StackEnt* stack = b.stacks + (size_t)blockIdx.x * kStackCap;
+    uint64_t* my_spl = b.spl + (size_t)blockIdx.x * (CAP / 2) * NW;
+    const int tid = threadIdx.x;
 
     for (;;) {
-        if (tid == 0) s_bucket = atomicAdd(ticket, 1u);
+        if (tid == 0) {
+            s_bucket = atomicAdd(&b.ctr[0], 1u);
+            s_sp = 0;
+            s_bad = 0;
+        }
         __syncthreads();
         const uint32_t c = s_bucket;
         if (c >= nbk) break;
-        const uint64_t base0 = boff[c];
-        const uint64_t end0 = boff[c + 1];
-        if (tid == 0) {
-            s_u = 0;
-            s_tbase = base0;
-            s_bad = 0;
-            s_sp = 0;
-            if (end0 > base0) {
-                stack[0] = StackEnt{(uint32_t)base0, (uint32_t)end0, bflags[c] ? SF_UNIFORM : 0u, 0u};
-                s_sp = 1;
-            }
+        if (tid < 32) {
+            const uint64_t base0 = boff[c], end0 = boff[c + 1];
+            route_range<Src, MODE, WL, Cfg::MCAP>(src, b, tid == 0, (uint32_t)base0, (uint32_t)(end0 - base0),
+                                            bflags[c] ? SF_UNIFORM : 0u, stack, &s_sp);
         }
         __syncthreads();
         uint32_t iters = 0;
         for (;;) {
             if (tid == 0) {
-                if (s_sp == 0 || s_bad) {
+                if (s_sp == 0 || s_bad || s_sp > (uint32_t)kStackCap) {
                     s_done = 1;
                 } else {
                     const StackEnt e = stack[--s_sp];
@@ -946,15 +1657,13 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
             __syncthreads();
             if (s_done) break;
             if (++iters > (1u << 24)) {
-                if (tid == 0) { atomicOr(err, ERR_ITER); s_bad = 1; }
-                __syncthreads();
+                if (tid == 0) atomicOr(b.err, ERR_ITER);
                 break;
             }
             const uint32_t lo = s_lo, hi = s_hi, fl = s_fl;
             const uint32_t n = hi - lo;
-            const uint64_t tout = s_tbase + s_u;
-            uint32_t* cur = (fl & SF_INB) ? recB : recA;
-            uint32_t* oth = (fl & SF_INB) ? recA : recB;
+            uint32_t* cur = (fl & SF_INB) ? b.recB : b.recA;
+            uint32_t* oth = (fl & SF_INB) ? b.recA : b.recB;
 
             if (fl & SF_UNIFORM) {
                 // ---- every record in the range has the same key
@@ -965,230 +1674,281 @@ __global__ void __launch_bounds__(kL2Threads) k_level2(
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc.shfl_merge(o);
-                if ((tid & 31) == 0) s_acc[tid >> 5] = acc;
+                if ((tid & 31) == 0) sh.acc[tid >> 5] = acc;
                 __syncthreads();
                 if (tid < 32) {
                     Acc<MODE> a2;
-                    if (tid < T / 32) a2 = s_acc[tid];
+                    if (tid < T / 32) a2 = sh.acc[tid];
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) a2.shfl_merge(o);
                     if (tid == 0) {
                         uint64_t k[NW];
                         src.key(cur[lo], k);
-                        key_store<NW>(Tkeys, tout, k);
-                        Tcoef[tout] = a2.result();
-                        s_u += 1;
+                        key_store<NW>(b.Tkeys, lo, k);
+                        b.Tcoef[lo] = a2.result();
+                        b.oflag[lo] = 1;
                     }
                 }
                 __syncthreads();
-            } else if (n <= CAP) {
-                // ---- leaf: keys and phases into shared memory, sort, then sum
-                // each run of equal keys with a block segmented scan
-                for (uint32_t t = tid; t < n; t += T) {
-                    uint64_t k[NW];
-                    const uint32_t r = cur[lo + t];
-                    rec_s[t] = r;
-                    ph_s[t] = (uint8_t)src.keyphase(r, k);
-                    skey_store<NW>(keys_s, CAP, t, k);
-                }
-                uint32_t size = 2u * (uint32_t)T >= 64u ? 64u : 2u * (uint32_t)T;
-                while (size < n) size <<= 1;
-                __syncthreads();
-                build_codes<NW, T, CAP>(c1s, keys_s, n, s_or, &s_L);
-                const uint16_t* srt = merge_sort_slots<NW, T, CAP>(ord_s, tmp_s, c1s, keys_s, n, size, rec_s);
-                // positions [p0, p0 + PP) of this thread, in sorted order
-                const uint32_t p0 = (uint32_t)tid * PP;
-                bool hd[PP];
-                V v[PP];
-                uint32_t sl[PP];
-                uint32_t nh = 0;
-#pragma unroll
-                for (uint32_t q = 0; q < PP; ++q) {
-                    const uint32_t p = p0 + q;
-                    hd[q] = false;
-                    if (act && p < n) {
-                        sl[q] = srt[p];
-                        v[q] = src.coefv(rec_s[sl[q]], ph_s[sl[q]]);
-                        hd[q] = (p == 0) || slot_key_neq<NW, CAP>(sl[q], srt[p - 1], c1s, keys_s);
-                        nh += hd[q] ? 1u : 0u;
-                    }
-                }
-                Acc<MODE> trail;
-#pragma unroll
-                for (uint32_t q = 0; q < PP; ++q) {
-                    if (act && p0 + q < n) {
-                        if (hd[q]) trail = Acc<MODE>();
-                        trail.add(v[q]);
-                    }
-                }
-                uint32_t total;
-                const uint32_t hex = block_excl_scan<T>(nh, s_warp, total);
-                Acc<MODE> run = block_seg_carry<T, MODE>(nh > 0, trail, s_acc, s_flag);
-                uint64_t oidx = (uint64_t)hex - 1;  // index of the run flowing in (if any)
-#pragma unroll
-                for (uint32_t q = 0; q < PP; ++q) {
-                    const uint32_t p = p0 + q;
-                    if (act && p < n) {
-                        if (hd[q]) {
-                            run = Acc<MODE>();
-                            ++oidx;
-                        }
-                        run.add(v[q]);
-                        bool last = p + 1 >= n;
-                        if (!last) {
-                            if (q + 1 < PP) last = hd[q + 1];
-                            else last = slot_key_neq<NW, CAP>(srt[p + 1], sl[q], c1s, keys_s);
-                        }
-                        if (last) {
-                            uint64_t k[NW];
-                            skey_load<NW>(keys_s, CAP, sl[q], k);
-                            key_store<NW>(Tkeys, tout + oidx, k);
-                            Tcoef[tout + oidx] = run.result();
-                        }
-                    }
-                }
-                __syncthreads();
-                if (tid == 0) s_u += total;
-                __syncthreads();
-            } else {
-                // ---- split: splitters from a sorted sample of this range
-                const uint32_t want = (uint32_t)mn<uint64_t>(CAP / 4, ((uint64_t)n + CAP / 2 - 1) / (CAP / 2));
-                uint32_t S = 64;
-                while (S < 16u * want && S < CAP) S <<= 1;
-                for (uint32_t t = tid; t < S; t += T) {
-                    const uint32_t pos = lo + (uint32_t)(((uint64_t)t * n) / S);
-                    uint64_t k[NW];
-                    src.key(cur[pos], k);
-                    skey_store<NW>(keys_s, CAP, t, k);
-                }
-                __syncthreads();
-                build_codes<NW, T, CAP>(c1s, keys_s, S, s_or, &s_L);
-                const uint16_t* srt = merge_sort_slots<NW, T, CAP>(ord_s, tmp_s, c1s, keys_s, S, S, nullptr);
-                uint8_t* fl_s = ph_s;  // flag of range b+1 follows splitter b
-                if (tid == 0) {
-                    uint32_t nsp = 0;
-                    fl_s[0] = 0;
-                    bool stop = false;
-                    // a key fills a uniform range when it covers half a target range of the sample
-                    const uint32_t heavy_min = mn<uint32_t>(S, S / (2u * want) > 2u ? S / (2u * want) : 2u);
-                    for (uint32_t t = 1; t < want && !stop; ++t) {
-                        const uint32_t rho = (uint32_t)(((uint64_t)t * S) / want);
-                        const uint32_t ci = srt[rho];
-                        uint64_t k[NW], s2[NW];
-                        skey_load<NW>(keys_s, CAP, ci, k);
-                        if (nsp > 0 && key_cmp_m<NW>(k, my_spl + (size_t)(nsp - 1) * NW) <= 0) continue;
-                        uint32_t r0 = rho, r1 = rho;
-                        while (r0 > 0 && !slot_key_neq<NW, CAP>(srt[r0 - 1], ci, c1s, keys_s)) --r0;
-                        while (r1 + 1 < S && !slot_key_neq<NW, CAP>(srt[r1 + 1], ci, c1s, keys_s)) ++r1;
-                        const bool heavy = r1 - r0 + 1 >= heavy_min;
-                        key_store<NW>(my_spl, nsp, k);
-                        ++nsp;
-                        fl_s[nsp] = heavy ? 1u : 0u;
-                        if (heavy) {
-                            if (key_succ<NW>(k, s2)) {
-                                key_store<NW>(my_spl, nsp, s2);
-                                ++nsp;
-                                fl_s[nsp] = 0;
-                            } else {
-                                stop = true;  // nothing sorts after the largest key
-                            }
-                        }
-                    }
-                    s_nsp = nsp;
-                }
-                __syncthreads();
-                const uint32_t nsp = s_nsp;
-                const uint32_t nbs = nsp + 1;
-                for (uint32_t q = tid; q < nsp * NW; q += T) keys_s[(q % NW) * (CAP / 2) + q / NW] = my_spl[q];
-                uint32_t* cnt = reinterpret_cast<uint32_t*>(c1s);  // [nbs]
-                uint32_t* cpos = cnt + CAP / 2;                      // [nbs]
-                for (uint32_t q = tid; q < nbs; q += T) { cnt[q] = 0; cpos[q] = 0; }
-                __syncthreads();
-                for (uint32_t idx = lo + tid; idx < hi; idx += T) {
-                    uint64_t k[NW];
-                    src.key(cur[idx], k);
-                    const uint32_t b = upper_bound_skeys<NW>(keys_s, CAP / 2, nsp, k);
-                    subid[idx] = (uint16_t)b;
-                    atomicAdd(&cnt[b], 1u);
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    uint32_t runc = 0;
-                    uint32_t bad = 0;
-                    for (uint32_t b = 0; b < nbs; ++b) {
-                        const uint32_t cb = cnt[b];
-                        if (cb == n && !(fl_s[b] & 1u)) bad = 1;  // no progress
-                        cnt[b] = runc;
-                        runc += cb;
-                    }
-                    if (bad) { atomicOr(err, ERR_PROGRESS); s_bad = 1; }
-                    else if (s_sp + nbs > (uint32_t)kStackCap) { atomicOr(err, ERR_STACK); s_bad = 1; }
-                }
-                __syncthreads();
-                if (!s_bad) {
-                    for (uint32_t idx = lo + tid; idx < hi; idx += T) {
-                        const uint32_t b = subid[idx];
-                        const uint32_t p = atomicAdd(&cpos[b], 1u);
-                        oth[lo + cnt[b] + p] = cur[idx];
-                    }
-                    __syncthreads();
-                    if (tid == 0) {
-                        const uint32_t inb = (fl & SF_INB) ? 0u : SF_INB;  // children live in the other buffer
-                        for (int b = (int)nbs - 1; b >= 0; --b) {
-                            const uint32_t s0 = cnt[b];
-                            const uint32_t s1 = (b + 1 < (int)nbs) ? cnt[b + 1] : n;
-                            if (s1 > s0)
-                                stack[s_sp++] = StackEnt{lo + s0, lo + s1, ((fl_s[b] & 1u) ? SF_UNIFORM : 0u) | inb, 0u};
-                        }
-                    }
-                }
-                __syncthreads();
+                continue;
             }
+            // ---- split: splitters from a sorted sample of this range
+            static_assert(CAP / 4 <= (uint32_t)T, "one splitter candidate per thread");
+            const uint32_t want = (uint32_t)mn<uint64_t>(
+                CAP / 4, ((uint64_t)n + child_target - 1) / child_target > 2 ? ((uint64_t)n + child_target - 1) / child_target : 2);
+            uint32_t S = 64;
+            while (S < 16u * want && S < CAP) S <<= 1;
+            for (uint32_t t = tid; t < S; t += T) {
+                const uint32_t pos = lo + (uint32_t)(((uint64_t)t * n) / S);
+                uint64_t k[NW];
+                src.key(cur[pos], k);
+                skey_store<NW>(keys_s, CAP, t, k);
+            }
+            __syncthreads();
+            build_codes<NW, T, CAP>(c1s, keys_s, S, sh.orr, &sh.L);
+            const uint16_t* srt = merge_sort_slots<NW, T, CAP>(ord_s, tmp_s, c1s, keys_s, S, S, nullptr);
+            // Candidate t (1 <= t < want) is the key at sample rank t*S/want.
+            // A candidate equal to the one before it adds nothing; a key whose
+            // run in the sample covers half a target range or more is heavy and
+            // adds the pair (key, successor), so that it gets a range of its own.
+            {
+                const uint32_t heavy_min = mn<uint32_t>(S, S / (2u * want) > 2u ? S / (2u * want) : 2u);
+                const uint32_t t = (uint32_t)tid + 1u;
+                uint32_t emit = 0;
+                bool heavy = false, has_succ = false;
+                uint64_t k[NW], s2[NW];
+                if (t < want) {
+                    const uint32_t rho = (uint32_t)(((uint64_t)t * S) / want);
+                    const uint32_t ci = srt[rho];
+                    const uint32_t rp = (uint32_t)(((uint64_t)(t - 1) * S) / want);
+                    if (t == 1 || slot_key_cmp<NW, CAP>(srt[rp], ci, c1s, keys_s) != 0) {
+                        skey_load<NW>(keys_s, CAP, ci, k);
+                        uint32_t a0 = 0, a1 = rho;  // first sample rank holding this key
+                        while (a0 < a1) {
+                            const uint32_t mid = (a0 + a1) >> 1;
+                            if (slot_key_cmp<NW, CAP>(srt[mid], ci, c1s, keys_s) < 0) a0 = mid + 1;
+                            else a1 = mid;
+                        }
+                        uint32_t b0 = rho, b1 = S - 1;  // last sample rank holding it
+                        while (b0 < b1) {
+                            const uint32_t mid = (b0 + b1 + 1) >> 1;
+                            if (slot_key_cmp<NW, CAP>(srt[mid], ci, c1s, keys_s) > 0) b1 = mid - 1;
+                            else b0 = mid;
+                        }
+                        heavy = b0 - a0 + 1 >= heavy_min;
+                        has_succ = heavy && key_succ<NW>(k, s2);
+                        emit = has_succ ? 2u : 1u;
+                    }
+                }
+                uint32_t nsp_total;
+                const uint32_t pos = block_excl_scan<T>(emit, sh.warp, nsp_total);
+                if (emit) {
+                    key_store<NW>(my_spl, pos, k);
+                    fl_s[pos + 1] = heavy ? 1u : 0u;  // [key, next splitter) holds only this key
+                    if (has_succ) {
+                        key_store<NW>(my_spl, pos + 1, s2);
+                        fl_s[pos + 2] = 0;
+                    }
+                }
+                if (tid == 0) {
+                    fl_s[0] = 0;
+                    s_done = nsp_total;  // splitter count, read after the barrier
+                }
+            }
+            __syncthreads();
+            const uint32_t nsp = s_done;
+            const uint32_t nbs = nsp + 1;
+            for (uint32_t q = tid; q < nsp * NW; q += T) keys_s[(q % NW) * (CAP / 2) + q / NW] = my_spl[q];
+            uint32_t* cnt = reinterpret_cast<uint32_t*>(c1s);    // [CAP / 2]
+            uint32_t* cpos = cnt + CAP / 2;                      // [CAP / 2]
+            uint64_t* sc = reinterpret_cast<uint64_t*>(cpos + CAP / 2);  // [CAP / 2] splitter codes
+            for (uint32_t q = tid; q < nbs; q += T) {
+                cnt[q] = 0;
+                cpos[q] = 0;
+            }
+            __syncthreads();
+            // The splitters share their first Ls bits.  A key whose first Ls
+            // bits differ from theirs lies below or above all of them; other
+            // keys are located by the 64 bits that follow (their code), with
+            // the whole key deciding only when a code equals a splitter's.
+            uint32_t Ls = 64u * NW;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                const uint64_t d = keys_s[(size_t)w * (CAP / 2)] ^ keys_s[(size_t)w * (CAP / 2) + nsp - 1];
+                if (d) {
+                    Ls = 64u * w + (uint32_t)__clzll((long long)d);
+                    break;
+                }
+            }
+            for (uint32_t q = tid; q < nsp; q += T) sc[q] = key_bits64<NW, CAP / 2>(keys_s, q, Ls);
+            __syncthreads();
+            for (uint32_t idx = lo + tid; idx < hi; idx += T) {
+                uint64_t k[NW];
+                src.key(cur[idx], k);
+                uint32_t bb;
+                const int pc = prefix_cmp<NW>(k, keys_s, CAP / 2, Ls);
+                if (pc != 0) {
+                    bb = pc < 0 ? 0u : nsp;
+                } else {
+                    const uint64_t code = reg_bits64<NW>(k, Ls);
+                    uint32_t l2 = 0, len = nsp;
+                    while (len > 0) {
+                        const uint32_t half = len >> 1, mid = l2 + half;
+                        const uint64_t sv = sc[mid];
+                        const bool ge = code != sv ? code > sv : skey_cmp_r<NW>(k, keys_s, CAP / 2, mid) >= 0;
+                        if (ge) {
+                            l2 = mid + 1;
+                            len -= half + 1;
+                        } else {
+                            len = half;
+                        }
+                    }
+                    bb = l2;
+                }
+                b.subid[idx] = (uint16_t)bb;
+                atomicAdd(&cnt[bb], 1u);
+            }
+            __syncthreads();
+            {  // exclusive scan of the child counts, in place; a child that got
+               // every record without being uniform means no progress
+                const uint32_t per = (nbs + T - 1) / T;
+                const uint32_t q0 = (uint32_t)tid * per;
+                uint32_t loc = 0;
+                for (uint32_t q = q0; q < q0 + per && q < nbs; ++q) {
+                    const uint32_t cb = cnt[q];
+                    if (cb == n && !(fl_s[q] & 1u)) s_bad = 1;
+                    loc += cb;
+                }
+                uint32_t tot;
+                uint32_t ex = block_excl_scan<T>(loc, sh.warp, tot);
+                for (uint32_t q = q0; q < q0 + per && q < nbs; ++q) {
+                    const uint32_t cb = cnt[q];
+                    cnt[q] = ex;
+                    ex += cb;
+                }
+            }
+            __syncthreads();
+            if (s_bad) {
+                if (tid == 0) atomicOr(b.err, ERR_PROGRESS);
+                continue;
+            }
+            for (uint32_t idx = lo + tid; idx < hi; idx += T) {
+                const uint32_t bb = b.subid[idx];
+                const uint32_t p = atomicAdd(&cpos[bb], 1u);
+                oth[lo + cnt[bb] + p] = cur[idx];
+            }
+            __syncthreads();
+            const uint32_t inb = (fl & SF_INB) ? 0u : SF_INB;  // children live in the other buffer
+            for (uint32_t q0 = 0; q0 < nbs; q0 += T) {
+                const uint32_t q = q0 + tid;
+                const bool valid = q < nbs;
+                uint32_t s0 = 0, s1 = 0, cf = 0;
+                if (valid) {
+                    s0 = cnt[q];
+                    s1 = q + 1 < nbs ? cnt[q + 1] : n;
+                    cf = ((fl_s[q] & 1u) ? SF_UNIFORM : 0u) | inb;
+                }
+                route_range<Src, MODE, WL, Cfg::MCAP>(src, b, valid, lo + s0, s1 - s0, cf, stack, &s_sp);
+            }
+            __syncthreads();
         }
-        if (tid == 0) ucount[c] = s_u;
-        __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------- compaction
+//
+// The flagged staging slots, in position order, are the merged terms.  The
+// flag array is split into chunks of kChunk slots; a count pass and a scan
+// give each chunk its first output index, and the copy kernels walk a chunk
+// with one block scan.
 
-template <int WP>
-__global__ void __launch_bounds__(256) k_compact(uint32_t nbk, const uint64_t* __restrict__ boff,
-                                                 const uint64_t* __restrict__ uoff,
-                                                 const uint64_t* __restrict__ Tkeys,
-                                                 const double2* __restrict__ Tcoef, uint64_t* okeys,
-                                                 double2* ocoef, uint8_t* opb) {
-    constexpr int NW = 2 * WP;
-    for (uint32_t c = blockIdx.x; c < nbk; c += gridDim.x) {
-        const uint64_t src0 = boff[c];
-        const uint64_t dst0 = uoff[c];
-        const uint64_t cnt = uoff[c + 1] - dst0;
-        for (uint64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
-            uint64_t k[NW];
-            key_load_g<NW>(Tkeys, src0 + t, k);
-            key_store<NW>(okeys, dst0 + t, k);
-            ocoef[dst0 + t] = Tcoef[src0 + t];
-            opb[dst0 + t] = (uint8_t)normal_phase<WP>(k, 0u);
+constexpr uint32_t kChunk = 8192;  // 256 threads x 32 flags
+constexpr int kChunkThreads = 256;
+
+static __global__ void __launch_bounds__(kChunkThreads) k_flag_count(const uint8_t* __restrict__ oflag, uint32_t nch,
+                                                              uint32_t* cnt) {
+    __shared__ uint32_t s_w[kChunkThreads / 32];
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        const uint4* f = reinterpret_cast<const uint4*>(oflag + (size_t)c * kChunk + (size_t)threadIdx.x * 32u);
+        const uint4 a = f[0], b2 = f[1];
+        // flags are 0 or 1 bytes: the bit count of a word is its flag count
+        uint32_t v = __popc(a.x) + __popc(a.y) + __popc(a.z) + __popc(a.w) + __popc(b2.x) + __popc(b2.y) +
+                     __popc(b2.z) + __popc(b2.w);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t s = 0;
+            for (int w = 0; w < kChunkThreads / 32; ++w) s += s_w[w];
+            cnt[c] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// Calls f(slot, output index) for every flagged slot of chunk c, in order
+// within each thread's 32 slots.  Called by the whole CTA.
+template <class F>
+__device__ __forceinline__ void for_each_flagged(uint32_t c, const uint8_t* __restrict__ oflag,
+                                                 const uint64_t* __restrict__ coff, uint32_t* s_warp, F&& f) {
+    const uint64_t p0 = (uint64_t)c * kChunk + (uint64_t)threadIdx.x * 32u;
+    const uint4* fp = reinterpret_cast<const uint4*>(oflag + p0);
+    const uint4 a = fp[0], b2 = fp[1];
+    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b2.x, b2.y, b2.z, b2.w};
+    uint32_t loc = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) loc += __popc(w[q]);
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan<kChunkThreads>(loc, s_warp, tot);
+    uint64_t r = coff[c] + ex;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        uint32_t m = w[q];
+        while (m) {
+            const int bit = __ffs(m) - 1;
+            f(p0 + (uint64_t)(q * 4 + (bit >> 3)), r);
+            ++r;
+            m &= m - 1u;
         }
     }
 }
 
-// Copies compacted (key, coefficient) pairs into dense scratch arrays (used
-// for the merged sample inside splitter selection).
-template <int NW>
-__global__ void k_compact_plain(uint32_t nbk, const uint64_t* __restrict__ boff,
-                                const uint64_t* __restrict__ uoff, const uint64_t* __restrict__ Tkeys,
-                                const double2* __restrict__ Tcoef, uint64_t* okeys, double2* ocoef) {
-    for (uint32_t c = blockIdx.x; c < nbk; c += gridDim.x) {
-        const uint64_t src0 = boff[c];
-        const uint64_t dst0 = uoff[c];
-        const uint64_t cnt = uoff[c + 1] - dst0;
-        for (uint64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+template <int WP>
+__global__ void __launch_bounds__(kChunkThreads) k_compact(uint32_t nch, const uint8_t* __restrict__ oflag,
+                                                         const uint64_t* __restrict__ coff,
+                                                         const uint64_t* __restrict__ Tkeys,
+                                                         const double2* __restrict__ Tcoef, uint64_t* okeys,
+                                                         double2* ocoef, uint8_t* opb) {
+    constexpr int NW = 2 * WP;
+    __shared__ uint32_t s_warp[32];
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        for_each_flagged(c, oflag, coff, s_warp, [&](uint64_t p, uint64_t d) {
             uint64_t k[NW];
-            key_load_g<NW>(Tkeys, src0 + t, k);
-            key_store<NW>(okeys, dst0 + t, k);
-            ocoef[dst0 + t] = Tcoef[src0 + t];
-        }
+            key_load_g<NW>(Tkeys, p, k);
+            key_store<NW>(okeys, d, k);
+            ocoef[d] = Tcoef[p];
+            opb[d] = (uint8_t)normal_phase<WP>(k, 0u);
+        });
+    }
+}
+
+// Copies the merged (key, coefficient) pairs into dense arrays (the merged
+// sample inside splitter selection).
+template <int NW>
+__global__ void __launch_bounds__(kChunkThreads) k_compact_plain(uint32_t nch, const uint8_t* __restrict__ oflag,
+                                                               const uint64_t* __restrict__ coff,
+                                                               const uint64_t* __restrict__ Tkeys,
+                                                               const double2* __restrict__ Tcoef, uint64_t* okeys,
+                                                               double2* ocoef) {
+    __shared__ uint32_t s_warp[32];
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        for_each_flagged(c, oflag, coff, s_warp, [&](uint64_t p, uint64_t d) {
+            uint64_t k[NW];
+            key_load_g<NW>(Tkeys, p, k);
+            key_store<NW>(okeys, d, k);
+            ocoef[d] = Tcoef[p];
+        });
     }
 }
 
@@ -1213,10 +1973,53 @@ static __global__ void k_or_err(const int32_t* inner, int32_t* outer) {
 }
 
 struct Staged {
-    // merged terms of every coarse range, dense within [boff[c], boff[c] + U_c)
-    Scratch Tkeys, Tcoef, boff, uoff, err;
-    uint32_t nbk = 0;
+    // merged terms at the flagged slots of Tkeys/Tcoef; the flagged slots of
+    // chunk c start at output index coff[c], and coff[nch] is their count
+    Scratch Tkeys, Tcoef, oflag, coff, err;
+    uint32_t nch = 0;
 };
+
+// Level 2, both leaf kernels, and the chunk offsets of the flagged slots.
+// b.oflag (nch * kChunk bytes), b.ctr (3 words) and b.err start at zero.
+template <class Src, int MODE>
+static void launch_level2(const Src& src, uint32_t nbk, const uint64_t* boff, const uint8_t* bflags, const L2Bufs& b,
+                          unsigned grid2, uint32_t nch, uint32_t* ccount, uint64_t* coff, cudaStream_t st) {
+    using Cfg = L2Cfg<Src, MODE>;
+    constexpr int NW = Src::NW;
+    constexpr uint32_t WL = warp_leaf_cap<NW>();
+    const int sms = device_sm_count();
+    {
+        StageScope ss(ST_LEVEL2, st);
+        auto k2 = k_level2<Src, MODE>;
+        smem_attr(k2, Cfg::SMEM);
+        note_launch(ST_LEVEL2);
+        k2<<<grid2, kL2Threads, Cfg::SMEM, st>>>(src, nbk, boff, bflags, b, (WL * 5) / 8);
+        check_cuda(cudaGetLastError(), "k_level2");
+    }
+    {
+        StageScope ss(ST_LEAF, st);
+        auto kb = k_leaf_block<Src, MODE>;
+        smem_attr(kb, Cfg::MSMEM);
+        const unsigned per_sm_b = (unsigned)std::max<size_t>(1, std::min<size_t>(8, (200u * 1024u) / Cfg::MSMEM));
+        note_launch(ST_LEAF);
+        kb<<<(unsigned)sms * per_sm_b, kLeafThreads, Cfg::MSMEM, st>>>(src, b);
+        check_cuda(cudaGetLastError(), "k_leaf_block");
+        auto kw = k_leaf_warp<Src, MODE>;
+        const size_t wsm = (size_t)kWarpLeafWarps * warp_leaf_bytes<NW>();
+        smem_attr(kw, wsm);
+        const unsigned per_sm = (unsigned)std::max<size_t>(1, std::min<size_t>(8, (200u * 1024u) / wsm));
+        note_launch(ST_LEAF);
+        kw<<<(unsigned)sms * per_sm, kWarpLeafWarps * 32, wsm, st>>>(src, b);
+        check_cuda(cudaGetLastError(), "k_leaf_warp");
+    }
+    StageScope ss(ST_COMPACT, st);
+    note_launch(ST_COMPACT);
+    note_launch(ST_COMPACT);
+    k_flag_count<<<std::max<uint32_t>(1, std::min<uint32_t>(nch, (uint32_t)sms * 8)), kChunkThreads, 0, st>>>(
+        b.oflag, nch, ccount);
+    k_scan_counts<<<1, 1024, 0, st>>>(ccount, nch, coff);
+    check_cuda(cudaGetLastError(), "flag scan");
+}
 
 template <class Src>
 struct IsProd : std::false_type {};
@@ -1239,10 +2042,10 @@ static void sorted_sample(const uint64_t* samp, uint32_t S, cudaStream_t st, Scr
     dc = Scratch((size_t)S * 16, st);
     du = Scratch(8, st);
     note_launch(ST_SAMPLE);
-    k_compact_plain<NW><<<std::min<uint32_t>(sg.nbk, 1024), 256, 0, st>>>(
-        sg.nbk, sg.boff.as<uint64_t>(), sg.uoff.as<uint64_t>(), sg.Tkeys.as<uint64_t>(),
-        sg.Tcoef.as<double2>(), dk.as<uint64_t>(), dc.as<double2>());
-    check_cuda(cudaMemcpyAsync(du.p, sg.uoff.as<uint64_t>() + sg.nbk, 8, cudaMemcpyDeviceToDevice, st),
+    k_compact_plain<NW><<<std::min<uint32_t>(sg.nch, 1024), kChunkThreads, 0, st>>>(
+        sg.nch, sg.oflag.as<uint8_t>(), sg.coff.as<uint64_t>(), sg.Tkeys.as<uint64_t>(), sg.Tcoef.as<double2>(),
+        dk.as<uint64_t>(), dc.as<double2>());
+    check_cuda(cudaMemcpyAsync(du.p, sg.coff.as<uint64_t>() + sg.nch, 8, cudaMemcpyDeviceToDevice, st),
                "sample count copy");
     check_cuda(cudaGetLastError(), "sample compaction");
     // the inner pipeline's error word joins the caller's (no host sync)
@@ -1270,20 +2073,20 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
         }
     }
     Scratch recA((size_t)Reff * 4, st), recB((size_t)Reff * 4, st), subid((size_t)R * 2, st);
-    Scratch bflags_s, cnt_s;
+    Scratch bflags_s, cnt_s, boff_s;
     uint32_t nbk = 1;
     const Tuning tune = tuning_for(NW);
     const uint64_t C1 = (uint64_t)CAP * (uint64_t)tune.coarse_factor;
 
     if (Reff <= C1) {
         StageScope ss(ST_SCATTER, st);
-        out.boff = Scratch(16, st);
+        boff_s = Scratch(16, st);
         bflags_s = Scratch(1, st);
         if (sym_na)
             k_iota_tri<<<(unsigned)((Reff + 255) / 256), 256, 0, st>>>(recA.as<uint32_t>(), (uint32_t)Reff, sym_na,
-                                                                     out.boff.as<uint64_t>(), bflags_s.as<uint8_t>());
+                                                                     boff_s.as<uint64_t>(), bflags_s.as<uint8_t>());
         else
-            k_iota<<<(R + 255) / 256, 256, 0, st>>>(recA.as<uint32_t>(), R, out.boff.as<uint64_t>(),
+            k_iota<<<(R + 255) / 256, 256, 0, st>>>(recA.as<uint32_t>(), R, boff_s.as<uint64_t>(),
                                                     bflags_s.as<uint8_t>());
         note_launch(ST_SCATTER);
         check_cuda(cudaGetLastError(), "k_iota");
@@ -1336,11 +2139,11 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
         check_cuda(cudaGetLastError(), "k_count");
         }
         StageScope ssx(ST_SCATTER, st);
-        out.boff = Scratch((size_t)(nbk + 1) * 8, st);
-        k_scan_counts<<<1, 1024, 0, st>>>(cnt_s.as<uint32_t>(), nbk, out.boff.as<uint64_t>());
+        boff_s = Scratch((size_t)(nbk + 1) * 8, st);
+        k_scan_counts<<<1, 1024, 0, st>>>(cnt_s.as<uint32_t>(), nbk, boff_s.as<uint64_t>());
         note_launch(ST_SCATTER);
         Scratch cursor((size_t)nbk * 8, st);
-        check_cuda(cudaMemcpyAsync(cursor.p, out.boff.p, (size_t)nbk * 8, cudaMemcpyDeviceToDevice, st), "cursor");
+        check_cuda(cudaMemcpyAsync(cursor.p, boff_s.p, (size_t)nbk * 8, cudaMemcpyDeviceToDevice, st), "cursor");
         const size_t sm = (size_t)((nbk + 1) & ~1u) * 4 + (size_t)nbk * 8;
         smem_attr(k_scatter, sm);
         const unsigned grid = (unsigned)std::max<uint64_t>(
@@ -1351,30 +2154,29 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
         check_cuda(cudaGetLastError(), "k_scatter");
     }
 
-    // level 2
-    out.nbk = nbk;
+    // level 2 and the leaves
+    constexpr uint32_t WL = warp_leaf_cap<NW>();
     out.Tkeys = Scratch((size_t)Reff * NW * 8, st);
     out.Tcoef = Scratch((size_t)Reff * 16, st);
-    Scratch ucount((size_t)nbk * 8, st), ticket(4, st);
-    check_cuda(cudaMemsetAsync(ticket.p, 0, 4, st), "memset");
+    out.nch = (uint32_t)((Reff + kChunk - 1) / kChunk);
+    out.oflag = Scratch((size_t)out.nch * kChunk, st);
+    out.coff = Scratch((size_t)(out.nch + 1) * 8, st);
+    Scratch ctr(16, st), ccount((size_t)out.nch * 4, st);
+    check_cuda(cudaMemsetAsync(out.oflag.p, 0, (size_t)out.nch * kChunk, st), "memset flags");
+    check_cuda(cudaMemsetAsync(ctr.p, 0, 16, st), "memset counters");
+    // every listed leaf holds at least two records (block leaves more than WL)
+    const uint32_t small_cap = (uint32_t)(Reff / 2 + 1), med_cap = (uint32_t)(Reff / (WL + 1) + 1);
+    Scratch lists(((size_t)small_cap + med_cap) * 8, st);
     const unsigned grid2 =
         (unsigned)std::max<uint32_t>(1, std::min<uint32_t>(nbk, (uint32_t)sms * (uint32_t)tune.range_ctas_per_sm));
     Scratch stacks((size_t)grid2 * kStackCap * sizeof(StackEnt), st);
     Scratch splscr((size_t)grid2 * (CAP / 2) * NW * 8, st);
-    auto k2 = k_level2<Src, MODE>;
-    smem_attr(k2, Cfg::SMEM);
-    StageScope ss2(ST_LEVEL2, st);
-    note_launch(ST_LEVEL2);
-    note_launch(ST_LEVEL2);  // k_level2 and the scan below
-    k2<<<grid2, kL2Threads, Cfg::SMEM, st>>>(src, nbk, out.boff.as<uint64_t>(), bflags_s.as<uint8_t>(),
-                                            recA.as<uint32_t>(), recB.as<uint32_t>(), subid.as<uint16_t>(),
-                                            ticket.as<uint32_t>(), stacks.as<StackEnt>(), splscr.as<uint64_t>(),
-                                            out.Tkeys.as<uint64_t>(), out.Tcoef.as<double2>(),
-                                            ucount.as<uint64_t>(), out.err.as<int32_t>());
-    check_cuda(cudaGetLastError(), "k_level2");
-    out.uoff = Scratch((size_t)(nbk + 1) * 8, st);
-    k_scan_u64<<<1, 1024, 0, st>>>(ucount.as<uint64_t>(), nbk, out.uoff.as<uint64_t>());
-    check_cuda(cudaGetLastError(), "k_scan_u64");
+    L2Bufs b{recA.as<uint32_t>(), recB.as<uint32_t>(), subid.as<uint16_t>(), ctr.as<uint32_t>(),
+             stacks.as<StackEnt>(), splscr.as<uint64_t>(), out.Tkeys.as<uint64_t>(), out.Tcoef.as<double2>(),
+             out.oflag.as<uint8_t>(), lists.as<uint2>(), lists.as<uint2>() + small_cap, small_cap, med_cap,
+             out.err.as<int32_t>()};
+    launch_level2<Src, MODE>(src, nbk, boff_s.as<uint64_t>(), bflags_s.as<uint8_t>(), b, grid2, out.nch,
+                             ccount.as<uint32_t>(), out.coff.as<uint64_t>(), st);
 }
 
 // Runs the pipeline and builds the output sum (one host synchronisation).
@@ -1384,7 +2186,7 @@ static paulib_sum* finish(const Src& src, uint32_t R, uint32_t nb_terms, int32_t
     Staged sg;
     run_pipeline<Src, MODE>(src, R, nb_terms, st, sg);
     struct { uint64_t u; int32_t e; } h{};
-    check_cuda(cudaMemcpyAsync(&h.u, sg.uoff.as<uint64_t>() + sg.nbk, 8, cudaMemcpyDeviceToHost, st), "U copy");
+    check_cuda(cudaMemcpyAsync(&h.u, sg.coff.as<uint64_t>() + sg.nch, 8, cudaMemcpyDeviceToHost, st), "U copy");
     check_cuda(cudaMemcpyAsync(&h.e, sg.err.p, 4, cudaMemcpyDeviceToHost, st), "err copy");
     check_cuda(cudaStreamSynchronize(st), "canonical sync");
     if (h.e) fail(PAULIB_ERR_INTERNAL, "canonicalisation failed on device (error word " + std::to_string(h.e) + ")");
@@ -1393,10 +2195,10 @@ static paulib_sum* finish(const Src& src, uint32_t R, uint32_t nb_terms, int32_t
     if (h.u > 0) {
         StageScope ss(ST_COMPACT, st);
         note_launch(ST_COMPACT);
-        const unsigned grid = std::max<uint32_t>(1, std::min<uint32_t>(sg.nbk, (uint32_t)device_sm_count() * 8));
-        k_compact<WP><<<grid, 256, 0, st>>>(sg.nbk, sg.boff.as<uint64_t>(), sg.uoff.as<uint64_t>(),
-                                           sg.Tkeys.as<uint64_t>(), sg.Tcoef.as<double2>(), out->keys, out->coef,
-                                           out->pbase);
+        const unsigned grid = std::max<uint32_t>(1, std::min<uint32_t>(sg.nch, (uint32_t)device_sm_count() * 8));
+        k_compact<WP><<<grid, kChunkThreads, 0, st>>>(sg.nch, sg.oflag.as<uint8_t>(), sg.coff.as<uint64_t>(),
+                                                     sg.Tkeys.as<uint64_t>(), sg.Tcoef.as<double2>(), out->keys,
+                                                     out->coef, out->pbase);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
             sum_free(out, st);

@@ -27,7 +27,7 @@ EXPORTED = ["paulib_abi_version", "paulib_sum_create", "paulib_sum_info", "pauli
             "paulib_last_error", "paulib_set_allocator", "paulib_timing_enable", "paulib_timing_read",
             "paulib_multiply_noalloc", "paulib_batch_plan_create", "paulib_batch_plan_launch",
             "paulib_batch_plan_outputs", "paulib_batch_plan_destroy", "paulib_set_tuning"]
-STAGES = ["convert", "sample", "count", "scatter", "level2", "compact", "raw", "export"]
+STAGES = ["convert", "sample", "count", "scatter", "level2", "compact", "raw", "export", "leaf"]
 
 
 class PaulibError(RuntimeError):
