@@ -404,20 +404,22 @@ constexpr int kL2Threads = 512;
 constexpr int kStackCap = 4096;
 constexpr int kSmemBudget = 110 * 1024;
 
-// Shared memory per leaf record: the product key (8*NW bytes), a sort code
-// (8 bytes), the record number (4 bytes, the tie-break that makes the order
-// of equal keys and so the summation order deterministic), two 16-bit slot
-// arrays for the merge sort and the product's phase exponent (1 byte).
-constexpr int kLeafRecBytes = 8 + 4 + 2 + 2 + 1;
+// Shared memory per sample slot of the range kernel: the key (8*NW bytes),
+// two sort codes (16 bytes), two 16-bit slot arrays for the merge sort and a
+// range flag (1 byte).  A block leaf slot adds the record number (4 bytes,
+// the tie-break that makes the order of equal keys and so the summation
+// order deterministic).  CAP is the sample capacity of the range kernel.
+constexpr int kSplitRecBytes = 16 + 2 + 2 + 1;
+constexpr int kBlockLeafRecBytes = kSplitRecBytes + 4;
 template <int NW>
 constexpr int leaf_cap() {
     int cap = 4096;
-    while (cap > 64 && cap * (8 * NW + kLeafRecBytes) > kSmemBudget) cap >>= 1;
+    while (cap > 64 && cap * (8 * NW + kSplitRecBytes) > kSmemBudget) cap >>= 1;
     return cap;
 }
 template <int NW>
 constexpr size_t leaf_smem() {
-    return (size_t)leaf_cap<NW>() * (8 * NW + kLeafRecBytes);
+    return (size_t)leaf_cap<NW>() * (8 * NW + kSplitRecBytes);
 }
 
 // Coarse (level 1) splitters live in shared memory of the counting kernel.
@@ -705,16 +707,19 @@ struct L2Cfg {
     static constexpr size_t SMEM = leaf_smem<NW>();
     // block leaves: at most MCAP records, sorted by one small CTA
     static constexpr uint32_t MCAP = CAP < 512 ? (uint32_t)CAP : 512u;
-    static constexpr size_t MSMEM = (size_t)MCAP * (8 * NW + kLeafRecBytes);
+    static constexpr size_t MSMEM = (size_t)MCAP * (8 * NW + kBlockLeafRecBytes);
 };
 
 // ---- leaf ordering
 //
-// A leaf (or a split sample) is ordered through one 64-bit code per slot:
-// the key bits that follow the common prefix L of every key in the range.
-// Equal codes fall back to the full keys and then to the record number, so
-// the order is total and deterministic.  Slots >= n are padding that sorts
-// last.
+// A block leaf (or a split sample) is ordered through two 64-bit codes per
+// slot, held as c1s[t] and c1s[CAP + t]: the 64 key bits from the first
+// position L where keys of the range differ, and the 64 from the first
+// position L2 >= L + 64 where they differ.  Keys agree on every position
+// outside those windows up to L2 + 64, so equal code pairs rarely hide
+// different keys; they fall back to the full keys and then to the record
+// number, so the order is total and deterministic.  Slots >= n are padding
+// that sorts last.
 
 template <int NW, uint32_t CAP>
 __device__ __forceinline__ bool slot_gt(uint32_t a, uint32_t b, const uint64_t* c1s, const uint64_t* keys_s,
@@ -722,6 +727,8 @@ __device__ __forceinline__ bool slot_gt(uint32_t a, uint32_t b, const uint64_t* 
     if (a >= n || b >= n) return a >= n && (b < n || a > b);
     const uint64_t ca = c1s[a], cb = c1s[b];
     if (ca != cb) return ca > cb;
+    const uint64_t da = c1s[CAP + a], db = c1s[CAP + b];
+    if (da != db) return da > db;
     const int c = skey_cmp<NW>(keys_s, CAP, a, b);
     if (c) return c > 0;
     if (recs) return recs[a] > recs[b];
@@ -730,7 +737,7 @@ __device__ __forceinline__ bool slot_gt(uint32_t a, uint32_t b, const uint64_t* 
 
 template <int NW, uint32_t CAP>
 __device__ __forceinline__ bool slot_key_neq(uint32_t a, uint32_t b, const uint64_t* c1s, const uint64_t* keys_s) {
-    if (c1s[a] != c1s[b]) return true;
+    if (c1s[a] != c1s[b] || c1s[CAP + a] != c1s[CAP + b]) return true;
     return skey_cmp<NW>(keys_s, CAP, a, b) != 0;
 }
 
@@ -744,8 +751,8 @@ __device__ __forceinline__ uint64_t key_bits64(const uint64_t* keys_s, uint32_t 
     return v;
 }
 
-// Codes c1s[0..n): the first bit L where any key differs from key 0 comes
-// from an OR reduction of (key ^ key 0) over the range.
+// Codes c1s[0..n) and c1s[CAP..CAP + n): the positions where keys differ
+// come from an OR reduction of (key ^ key 0) over the range.
 template <int NW, int T, uint32_t CAP>
 __device__ void build_codes(uint64_t* c1s, const uint64_t* keys_s, uint32_t n, unsigned long long* s_or,
                             uint32_t* s_L) {
@@ -767,14 +774,24 @@ __device__ void build_codes(uint64_t* c1s, const uint64_t* keys_s, uint32_t n, u
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t L = 64u * NW;
+        uint32_t L = 64u * NW, L2 = 64u * NW;
         for (int w = 0; w < NW; ++w)
             if (s_or[w]) { L = 64u * w + (uint32_t)__clzll((long long)s_or[w]); break; }
-        *s_L = L;
+        for (int w = 0; w < NW; ++w) {
+            if (64u * w + 63u < L + 64u) continue;
+            uint64_t mm = s_or[w];
+            if (L + 64u > 64u * w) mm &= ~0ull >> (L + 64u - 64u * w);
+            if (mm) { L2 = 64u * w + (uint32_t)__clzll((long long)mm); break; }
+        }
+        s_L[0] = L;
+        s_L[1] = L2;
     }
     __syncthreads();
-    const uint32_t L = *s_L;
-    for (uint32_t t = threadIdx.x; t < n; t += T) c1s[t] = key_bits64<NW, CAP>(keys_s, t, L);
+    const uint32_t L = s_L[0], L2 = s_L[1];
+    for (uint32_t t = threadIdx.x; t < n; t += T) {
+        c1s[t] = key_bits64<NW, CAP>(keys_s, t, L);
+        c1s[CAP + t] = key_bits64<NW, CAP>(keys_s, t, L2);
+    }
     __syncthreads();
 }
 
@@ -918,6 +935,8 @@ template <int NW, uint32_t CAP>
 __device__ __forceinline__ int slot_key_cmp(uint32_t a, uint32_t b, const uint64_t* c1s, const uint64_t* keys_s) {
     const uint64_t ca = c1s[a], cb = c1s[b];
     if (ca != cb) return ca < cb ? -1 : 1;
+    const uint64_t da = c1s[CAP + a], db = c1s[CAP + b];
+    if (da != db) return da < db ? -1 : 1;
     return skey_cmp<NW>(keys_s, CAP, a, b);
 }
 
@@ -928,7 +947,7 @@ struct BlockShared {
     Acc<MODE> acc[32];
     uint32_t flag[32];
     unsigned long long orr[NW];
-    uint32_t L;
+    uint32_t L[2];
 };
 
 // Device buffers of level 2.  Merged terms are written at the record
@@ -962,8 +981,8 @@ __device__ void block_leaf(const Src& src, const uint32_t* cur, uint32_t lo, uin
     constexpr uint32_t ACT = CAP < (uint32_t)T ? CAP : (uint32_t)T;
     constexpr uint32_t PP = CAP / ACT;  // sorted positions per active thread
     uint64_t* keys_s = reinterpret_cast<uint64_t*>(smem);        // [NW][CAP]
-    uint64_t* c1s = keys_s + (size_t)CAP * NW;                   // [CAP]
-    uint32_t* rec_s = reinterpret_cast<uint32_t*>(c1s + CAP);    // [CAP]
+    uint64_t* c1s = keys_s + (size_t)CAP * NW;                   // [2][CAP] codes
+    uint32_t* rec_s = reinterpret_cast<uint32_t*>(c1s + 2 * CAP);  // [CAP]
     uint16_t* ord_s = reinterpret_cast<uint16_t*>(rec_s + CAP);  // [CAP]
     uint16_t* tmp_s = ord_s + CAP;                               // [CAP]
     uint8_t* ph_s = reinterpret_cast<uint8_t*>(tmp_s + CAP);     // [CAP]
@@ -979,7 +998,7 @@ __device__ void block_leaf(const Src& src, const uint32_t* cur, uint32_t lo, uin
     uint32_t size = 64u;
     while (size < n) size <<= 1;
     __syncthreads();
-    build_codes<NW, T, CAP>(c1s, keys_s, n, sh.orr, &sh.L);
+    build_codes<NW, T, CAP>(c1s, keys_s, n, sh.orr, sh.L);
     const uint16_t* srt = merge_sort_slots<NW, T, CAP>(ord_s, tmp_s, c1s, keys_s, n, size, rec_s);
     const uint32_t p0 = (uint32_t)tid * PP;
     bool hd[PP];
@@ -1191,16 +1210,31 @@ __device__ __forceinline__ bool warp_heads(const WE (&x)[EPL], bool (&hd)[EPL], 
     return false;
 }
 
+// Value of slot s from the gather layout (slot t lives in row t/32 of lane
+// t%32).  Called by all lanes.
+template <class V, uint32_t EPL>
+__device__ __forceinline__ V fetch_v(const V (&vr)[EPL], uint32_t s) {
+    V out = vr[0];
+    const int srcl = (int)(s & 31u);
+#pragma unroll
+    for (uint32_t r = 0; r < EPL; ++r) {
+        V t;
+        t.x = __shfl_sync(0xffffffffu, vr[r].x, srcl);
+        t.y = __shfl_sync(0xffffffffu, vr[r].y, srcl);
+        if (r == (s >> 5)) out = t;
+    }
+    return out;
+}
+
 // Segmented sums of the sorted entries' values over runs of equal keys.
 // DIRECT writes each run's term to slot lo + (run index); otherwise the run
 // total stays in acc[e] at the run's last position and repl[run index]
 // records (slot | position << 8) of that position.  Returns the run count.
 template <class Src, int MODE, int NW, uint32_t WL, uint32_t EPL, bool DIRECT>
-__device__ __forceinline__ uint32_t warp_run_sums(const Src& src, const WE (&x)[EPL], const bool (&hd)[EPL],
-                                                  Acc<MODE> (&acc)[EPL], uint32_t lane, uint32_t n, uint32_t lo,
-                                                  const uint64_t* wk, const uint32_t* wr, const uint8_t* wp,
-                                                  uint16_t* repl, uint64_t* Tkeys, double2* Tcoef,
-                                                  uint8_t* oflag) {
+__device__ __forceinline__ uint32_t warp_run_sums(const typename Src::V (&vr)[EPL], const WE (&x)[EPL],
+                                                  const bool (&hd)[EPL], Acc<MODE> (&acc)[EPL], uint32_t lane,
+                                                  uint32_t n, uint32_t lo, const uint64_t* wk, uint16_t* repl,
+                                                  uint64_t* Tkeys, double2* Tcoef, uint8_t* oflag) {
     Acc<MODE> carry;
     uint32_t heads_before = 0;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -1209,7 +1243,8 @@ __device__ __forceinline__ uint32_t warp_run_sums(const Src& src, const WE (&x)[
         const uint32_t g = e * 32u + lane;
         const bool valid = g < n;
         Acc<MODE> a;
-        if (valid) a.add(src.coefv(wr[x[e].s], wp[x[e].s]));
+        const typename Src::V v = fetch_v<typename Src::V, EPL>(vr, x[e].s);
+        if (valid) a.add(v);
         bool f = hd[e];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1330,7 +1365,7 @@ __device__ __forceinline__ uint64_t key_hash(const uint64_t (&k)[NW]) {
         h = (h ^ k[w]) * 0x9e3779b97f4a7c15ull;
         h ^= h >> 29;
     }
-    return h;
+    return mix64(h);
 }
 
 // One warp leaf of n <= 32*EPL records.  Phase 1 sorts (key hash, record),
@@ -1344,21 +1379,24 @@ template <class Src, int MODE, int NW, uint32_t WL, uint32_t EPL>
 __device__ void warp_leaf_rows(const Src& src, const uint32_t* cur, uint32_t lo, uint32_t n, unsigned char* wsm,
                                uint64_t* Tkeys, double2* Tcoef, uint8_t* oflag) {
     static_assert(EPL * 32 <= WL && WL <= 128, "network fits the slice");
+    using V = typename Src::V;
     uint64_t* wk = reinterpret_cast<uint64_t*>(wsm);                   // [NW][WL]
     uint32_t* wr = reinterpret_cast<uint32_t*>(wk + (size_t)NW * WL);  // [WL]
     uint16_t* repl = reinterpret_cast<uint16_t*>(wr + WL);             // [WL]
-    uint8_t* wp = reinterpret_cast<uint8_t*>(repl + WL);               // [WL]
     const uint32_t lane = threadIdx.x & 31u;
     uint64_t hh[EPL];
+    V vr[EPL];  // each record's value, in the gather layout
 #pragma unroll
     for (uint32_t e = 0; e < EPL; ++e) {
         const uint32_t t = e * 32u + lane;
         hh[e] = ~0ull;
+        vr[e].x = 0;
+        vr[e].y = 0;
         if (t < n) {
             uint64_t k[NW];
             const uint32_t r = cur[lo + t];
             wr[t] = r;
-            wp[t] = (uint8_t)src.keyphase(r, k);
+            vr[e] = src.value(r, k);
             skey_store<NW>(wk, WL, t, k);
             hh[e] = key_hash<NW>(k);
         } else {
@@ -1399,8 +1437,8 @@ __device__ void warp_leaf_rows(const Src& src, const uint32_t* cur, uint32_t lo,
     }
     warp_sort<NW, WL, EPL, 1, false>(x, lane, wk, wr, 0);
     if (!warp_heads<NW, WL, EPL, 1, true>(x, hd, lane, n, wk, wl0)) {
-        const uint32_t U = warp_run_sums<Src, MODE, NW, WL, EPL, false>(src, x, hd, acc, lane, n, lo, wk, wr, wp,
-                                                                         repl, Tkeys, Tcoef, oflag);
+        const uint32_t U = warp_run_sums<Src, MODE, NW, WL, EPL, false>(vr, x, hd, acc, lane, n, lo, wk, repl,
+                                                                         Tkeys, Tcoef, oflag);
         __syncwarp();
         if (U <= 32u) {
             warp_phase2_k<Src, MODE, NW, WL, 1, EPL>(K, acc, U, lane, lo, wk, repl, L, L2, w0, Tkeys, Tcoef, oflag);
@@ -1424,7 +1462,7 @@ __device__ void warp_leaf_rows(const Src& src, const uint32_t* cur, uint32_t lo,
     }
     warp_sort<NW, WL, EPL, 3, false>(x, lane, wk, wr, w0);
     warp_heads<NW, WL, EPL, 3, false>(x, hd, lane, n, wk, w0);
-    warp_run_sums<Src, MODE, NW, WL, EPL, true>(src, x, hd, acc, lane, n, lo, wk, wr, wp, repl, Tkeys, Tcoef, oflag);
+    warp_run_sums<Src, MODE, NW, WL, EPL, true>(vr, x, hd, acc, lane, n, lo, wk, repl, Tkeys, Tcoef, oflag);
     __syncwarp();
 }
 
@@ -1472,17 +1510,17 @@ constexpr uint32_t kUniformWarpMax = 4096;  // longest all-equal range summed by
 constexpr int kWarpLeafWarps = 8;   // warps per CTA of the warp-leaf kernel
 
 // Warp-leaf capacity: up to 128 records, with each warp's slice of shared
-// memory (keys, record numbers, phases) kept within 5.5 KB so that many warps
+// memory (keys, record numbers, run list) kept within 5.5 KB so that many warps
 // stay resident (the leaf is bound by latency, not bandwidth).
 template <int NW>
 constexpr uint32_t warp_leaf_cap() {
     uint32_t wl = 128;
-    while (wl > 32 && wl * (8u * NW + 7u) > 5632u) wl >>= 1;
+    while (wl > 32 && wl * (8u * NW + 6u) > 5632u) wl >>= 1;
     return wl;
 }
 template <int NW>
 constexpr size_t warp_leaf_bytes() {
-    return ((size_t)warp_leaf_cap<NW>() * (8 * NW + 7) + 15) & ~(size_t)15;
+    return ((size_t)warp_leaf_cap<NW>() * (8 * NW + 6) + 15) & ~(size_t)15;
 }
 
 template <class Src, int MODE>
@@ -1615,8 +1653,8 @@ __global__ void __launch_bounds__(kL2Threads, 2) k_level2(Src src, uint32_t nbk,
     constexpr int T = kL2Threads;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* keys_s = reinterpret_cast<uint64_t*>(smem);        // [NW][CAP]
-    uint64_t* c1s = keys_s + (size_t)CAP * NW;                   // [CAP]
-    uint16_t* ord_s = reinterpret_cast<uint16_t*>(c1s + CAP);    // [CAP]
+    uint64_t* c1s = keys_s + (size_t)CAP * NW;                   // [2][CAP] codes
+    uint16_t* ord_s = reinterpret_cast<uint16_t*>(c1s + 2 * CAP);  // [CAP]
     uint16_t* tmp_s = ord_s + CAP;                               // [CAP]
     uint8_t* fl_s = reinterpret_cast<uint8_t*>(tmp_s + CAP);     // [CAP]: flag of range p+1 follows splitter p
     __shared__ BlockShared<MODE, NW> sh;
@@ -1705,7 +1743,7 @@ __global__ void __launch_bounds__(kL2Threads, 2) k_level2(Src src, uint32_t nbk,
                 skey_store<NW>(keys_s, CAP, t, k);
             }
             __syncthreads();
-            build_codes<NW, T, CAP>(c1s, keys_s, S, sh.orr, &sh.L);
+            build_codes<NW, T, CAP>(c1s, keys_s, S, sh.orr, sh.L);
             const uint16_t* srt = merge_sort_slots<NW, T, CAP>(ord_s, tmp_s, c1s, keys_s, S, S, nullptr);
             // Candidate t (1 <= t < want) is the key at sample rank t*S/want.
             // A candidate equal to the one before it adds nothing; a key whose
@@ -1887,30 +1925,33 @@ static __global__ void __launch_bounds__(kChunkThreads) k_flag_count(const uint8
     }
 }
 
-// Calls f(slot, output index) for every flagged slot of chunk c, in order
-// within each thread's 32 slots.  Called by the whole CTA.
+// Calls f(slot, output index) for every flagged slot of chunk c.  Warp w
+// walks slots [c*kChunk + 1024w, +1024) in rows of 32 consecutive slots, so
+// that reads of the staging arrays and writes of the output are coalesced.
+// Called by the whole CTA.
 template <class F>
 __device__ __forceinline__ void for_each_flagged(uint32_t c, const uint8_t* __restrict__ oflag,
                                                  const uint64_t* __restrict__ coff, uint32_t* s_warp, F&& f) {
-    const uint64_t p0 = (uint64_t)c * kChunk + (uint64_t)threadIdx.x * 32u;
-    const uint4* fp = reinterpret_cast<const uint4*>(oflag + p0);
-    const uint4 a = fp[0], b2 = fp[1];
-    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b2.x, b2.y, b2.z, b2.w};
-    uint32_t loc = 0;
+    static_assert(kChunk == 1024u * (kChunkThreads / 32), "one 1024-slot segment per warp");
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const uint64_t base = (uint64_t)c * kChunk + (uint64_t)w * 1024u;
+    uint32_t mask = 0;  // bit i: slot base + 32i + lane is flagged
 #pragma unroll
-    for (int q = 0; q < 8; ++q) loc += __popc(w[q]);
-    uint32_t tot;
-    const uint32_t ex = block_excl_scan<kChunkThreads>(loc, s_warp, tot);
-    uint64_t r = coff[c] + ex;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        uint32_t m = w[q];
-        while (m) {
-            const int bit = __ffs(m) - 1;
-            f(p0 + (uint64_t)(q * 4 + (bit >> 3)), r);
-            ++r;
-            m &= m - 1u;
-        }
+    for (int i = 0; i < 32; ++i) mask |= (uint32_t)(oflag[base + (uint64_t)i * 32u + lane] != 0) << i;
+    const uint32_t wtot = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(mask));
+    __syncthreads();  // s_warp may still be read for the previous chunk
+    if (lane == 0) s_warp[w] = wtot;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (uint32_t q = 0; q < w; ++q) wbase += s_warp[q];
+    uint64_t r = coff[c] + wbase;
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) {
+        const bool fl = (mask >> i) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, fl);
+        if (fl) f(base + (uint64_t)i * 32u + lane, r + (uint32_t)__popc(bal & lt));
+        r += (uint32_t)__popc(bal);
     }
 }
 
