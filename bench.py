@@ -30,6 +30,11 @@ HBM_PEAK_FALLBACK = 6800.0
 # FP64 peak derived from unit counts: 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 
+# DRAM bytes (read + write) per product of a stage's kernels, from ncu
+# counters on the n=200, 6,000-term case scaled by product count; keyed by
+# (stage, n_qubits).  Set to None when the kernels change.
+TRAFFIC_PER_PRODUCT = {}
+
 WORKLOADS = {
     "jw_hh_n200_m30000": dict(n=200, m=30000, seed=401),
     "jw_hh_n100_m20000": dict(n=100, m=20000, seed=301),
@@ -166,6 +171,109 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU leg
+
+def timed_events(fn, stream, flush, reps, warm=2):
+    """Mean device time (ms) of fn() between CUDA events on `stream`, with L2
+    flushed before each timed call; fn returns an object with close()."""
+    import torch
+    for _ in range(warm):
+        fn().close()
+    ts = []
+    for k in range(reps):
+        flush.fill_(k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        o = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        o.close()
+    return statistics.mean(ts)
+
+
+def measure_outer_product(paulib, gh, gh2, h, stream, flush, reps, hbm_peak, peak_src):
+    """The raw outer product alone (every pair's key, exact phase and
+    coefficient, written at j*|A| + i): an HBM-write-bound kernel."""
+    W = h.x.shape[0]
+    WP = 1
+    while WP < W:
+        WP *= 2
+    products = h.m * h.m
+    ms = timed_events(lambda: paulib.multiply(gh, gh2, "fp64", canonical=False), stream, flush, reps)
+    # compulsory bytes: the product records written (2*WP key words, complex128,
+    # the X^x Z^z phase byte and the stored phase byte); the inputs are read once
+    bytes_out = products * (16 * WP + 16 + 2)
+    bytes_in = 2 * h.m * (16 * WP + 16 + 1)
+    gbs = (bytes_out + bytes_in) / (ms / 1e3) / 1e9
+    return {"ms_per_step": ms, "value": products / (ms / 1e3), "unit": UNIT,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": gbs / hbm_peak, "peak_source": peak_src,
+                         "bytes_per_product": 16 * WP + 16 + 2}}
+
+
+def measure_batched(paulib, stream, flush, reps, problems=4096):
+    """Batched products (4,096 independent sum x sum products shaped like
+    Pauli-propagation steps) as one prepared plan replayed from a CUDA graph,
+    against the plain FP64 form: one paulib_multiply call per product."""
+    import torch
+    from paper_2605_25974_gb300 import workloads as wl
+    t0 = time.perf_counter()
+    pairs = wl.batch(problems=problems)
+    gen_s = time.perf_counter() - t0
+    As = [paulib.PauliSum.from_arrays(a) for a, _ in pairs]
+    Bs = [paulib.PauliSum.from_arrays(b) for _, b in pairs]
+    products = int(sum(a.m * b.m for a, b in pairs))
+    res = {"problems": problems, "products": products, "n_qubits": pairs[0][0].n,
+           "generation_s": gen_s}
+    for prec in ("fp32_fp64merge", "fp64"):
+        plan = paulib.BatchPlan(As, Bs, prec, stream=stream)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                plan.launch(stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        ts = []
+        cur = torch.cuda.current_stream()
+        for k in range(reps):
+            flush.fill_(k)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(cur)
+            g.replay()
+            e1.record(cur)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.mean(ts)
+        outs = plan.outputs(stream=cur)
+        res["graph_" + prec] = {"ms_per_step": ms, "value": products / (ms / 1e3),
+                                "distinct_out": int(sum(o.n_terms for o in outs))}
+        del outs
+        plan.close()
+        del g
+    # plain FP64 form: one canonical multiply per product, back to back
+    torch.cuda.synchronize()
+    for i in range(min(64, problems)):
+        paulib.multiply(As[i], Bs[i], "fp64").close()
+    torch.cuda.synchronize()
+    flush.fill_(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(problems):
+        paulib.multiply(As[i], Bs[i], "fp64").close()
+    torch.cuda.synchronize()
+    seq_ms = (time.perf_counter() - t0) * 1e3
+    res["sequential_fp64"] = {"ms_per_step": seq_ms, "value": products / (seq_ms / 1e3),
+                              "note": "one paulib_multiply per product; each call synchronises once"}
+    res["speedup_vs_sequential_fp64"] = seq_ms / res["graph_fp32_fp64merge"]["ms_per_step"]
+    res["speedup_fp64_graph_vs_sequential_fp64"] = seq_ms / res["graph_fp64"]["ms_per_step"]
+    for t in As + Bs:
+        t.close()
+    return res
+
 
 def run_ours(args):
     import numpy as np
@@ -317,35 +425,47 @@ def run_ours(args):
     h2d = hx.numel() * 8 + hz.numel() * 8 + hc.numel() * 8
     d2h = (ox.numel() + oz.numel() + oc.numel()) * 8
 
-    # ---- roofline of the dominant stage
+    # ---- roofline of the dominant stage: compulsory HBM bytes that stage
+    # must move per step, over the stage's device time (CUDA events recorded
+    # on the launching stream around the stage's kernels)
     hbm_peak, peak_src = measured_peaks()
     dom = max(stage_ms, key=lambda s: stage_ms[s])
     dom_ms = stage_ms[dom] / args.steps
     WP = 1
     while WP < W:
         WP *= 2
-    if dom == "level2":
-        # compulsory traffic of the range kernel: read each record (4 B) and
-        # write each merged term once (2*WP words + complex128) to staging
-        bytes_per = products * 4 + U * (16 * WP + 16)
-        flops = products * 6 + 2 * (products - U)
-        t_hbm = bytes_per / (hbm_peak * 1e9)
-        t_fp = flops / (FP64_PEAK_TFLOPS * 1e12)
-        if t_fp > t_hbm:
-            roof = {"bound": "alu", "achieved": flops / (dom_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "peak_source": "derived FP64 (2 DFMA/clk/SM x 152 SMs x 2.07 GHz)"}
-        else:
-            roof = {"bound": "hbm", "achieved": bytes_per / (dom_ms / 1e3) / 1e9, "peak": hbm_peak,
-                    "unit": "GB/s", "peak_source": peak_src}
-    else:
-        bytes_per = products * 4
-        roof = {"bound": "hbm", "achieved": bytes_per / (dom_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                "peak_source": peak_src}
+    term_bytes = 16 * WP + 16 + 1  # key words, complex128, phase byte
+    stage_bytes = {
+        "count": products * 2,                       # one bucket id per product
+        "scatter": products * (2 + 4),               # bucket id in, record out
+        "level2": products * (4 + 2 + 4),            # one split pass: record in, child id, record out
+        "leaf": products * 4 + U * term_bytes,       # records in, merged terms out
+        "compact": products + U * (term_bytes + 16 * WP + 16),  # flags, staged terms in, terms out
+    }
+    bytes_per = stage_bytes.get(dom, products * 4)
+    roof = {"bound": "hbm", "achieved": bytes_per / (dom_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+            "peak_source": peak_src, "kernel": dom, "bytes_per_step": bytes_per}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
-    roof["kernel"] = dom
+    roof["traffic"] = TRAFFIC_PER_PRODUCT.get((dom, h.n)) and TRAFFIC_PER_PRODUCT[(dom, h.n)] * products
+    if dom in ("leaf", "level2"):
+        # these stages gather both factors' key words (and, in the leaf, the
+        # coefficients) from L2-resident tables: bound by L2 gathers and latency
+        gathered = products * 2 * (16 * WP + (16 if dom == "leaf" else 0))
+        roof["l2_gather_bytes"] = gathered
+        roof["l2_gather_GBs"] = gathered / (dom_ms / 1e3) / 1e9
     roof["kernel_ms_per_step"] = dom_ms
     roof["stage_ms_per_step"] = {k: v / args.steps for k, v in stage_ms.items()}
+    # whole-step bound of the method (compulsory traffic only: inputs once,
+    # merged terms once; the sort's intermediate traffic is overhead)
+    t_hbm = (2 * h.m * term_bytes + U * term_bytes) / (hbm_peak * 1e9)
+    t_fp = products * 8 / (FP64_PEAK_TFLOPS * 1e12)
+    roof["step_bound_ms"] = 1e3 * max(t_hbm, t_fp)
+    roof["step_frac"] = roof["step_bound_ms"] / ms
+
+    outer = measure_outer_product(paulib, gh, gh2, h, stream, flush, max(2, args.steps // 2), hbm_peak, peak_src)
+    batched = None
+    if not args.no_batched:
+        batched = measure_batched(paulib, stream, flush, max(3, args.steps // 2))
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -353,7 +473,8 @@ def run_ours(args):
             "config": {"workload": args.workload, "n_qubits": h.n, "terms": h.m, "products": products,
                        "distinct_out": U, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "512 MiB flush between timed steps"},
-            "roofline": roof, "precision": precision, "symmetric": symmetric,
+            "roofline": roof, "outer_product": outer, "precision": precision, "symmetric": symmetric,
+            "batched": batched,
             "e2e": {"value": products / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
             "gpu_launches": int(sum(stage_launches.values())),
@@ -377,6 +498,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="jw_hh_n200_m30000", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-products leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

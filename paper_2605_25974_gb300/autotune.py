@@ -32,7 +32,7 @@ SPACE = {
     "count_ctas_per_sm": [2, 4, 8],
     "range_ctas_per_sm": [1, 2],
 }
-DEFAULT = {"coarse_factor": 16, "oversample": 32, "count_ctas_per_sm": 4, "range_ctas_per_sm": 2}
+DEFAULT = {"coarse_factor": 32, "oversample": 32, "count_ctas_per_sm": 4, "range_ctas_per_sm": 2}
 
 
 def _key_words(n_qubits: int, batched: bool = False) -> int:

@@ -94,8 +94,10 @@ void launch_export(const paulib_sum* s, uint64_t* x_soa, uint64_t* z_soa, double
 //
 // CTA tile: RA = blockDim.x left terms (one per thread, held in registers)
 // times CB right terms staged in shared memory and read as warp broadcasts.
-// Consecutive threads write consecutive output indices j*|A| + i, so each
-// warp's stores are contiguous.
+// Consecutive threads own consecutive output indices j*|A| + i.  A warp's 32
+// product keys pass through a padded shared buffer and are written as
+// contiguous 16-byte pieces (one 512-byte segment per store instruction);
+// coefficients and phase bytes are contiguous per warp as they are.
 constexpr int kRawThreads = 128;
 constexpr int kRawCols = 32;
 
@@ -106,14 +108,19 @@ __global__ void __launch_bounds__(kRawThreads) k_outer_raw(
     const double2* __restrict__ bc, const uint8_t* __restrict__ bp, uint64_t* ok, double2* oc,
     uint8_t* oph, uint8_t* opb) {
     constexpr int NW = 2 * WP;
+    constexpr int KS = NW + 1;  // padded key stride in the staging buffer (words)
     __shared__ __align__(16) uint64_t sk[kRawCols * NW];
     __shared__ double2 sc[kRawCols];
     __shared__ uint32_t sp[kRawCols];
+    __shared__ uint64_t stage[kRawThreads / 32][32 * KS];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint64_t* ws = stage[warp];
     const int64_t tiles_i = (na + kRawThreads - 1) / kRawThreads;
     const int64_t tiles_j = (nb + kRawCols - 1) / kRawCols;
     for (int64_t tile = blockIdx.x; tile < tiles_i * tiles_j; tile += gridDim.x) {
         const int64_t ti = tile % tiles_i, tj = tile / tiles_i;
         const int64_t i = ti * kRawThreads + threadIdx.x;
+        const int64_t i0 = ti * kRawThreads + warp * 32;  // first row of this warp
         const int64_t j0 = tj * kRawCols;
         const int ncols = (int)mn<int64_t>(kRawCols, nb - j0);
         __syncthreads();
@@ -123,20 +130,41 @@ __global__ void __launch_bounds__(kRawThreads) k_outer_raw(
             sp[q] = bp[j0 + q];
         }
         __syncthreads();
-        if (i >= na) continue;
+        if (i0 >= na) continue;  // the whole warp is past the last row
+        const bool live = i < na;
+        const uint32_t nrow = (uint32_t)mn<int64_t>(32, na - i0);  // rows of this warp
         uint64_t a[NW];
-        key_load_g<NW>(ak, (uint64_t)i, a);
-        const double2 ca = ac[i];
-        const uint32_t pa = ap[i];
+        double2 ca = make_double2(0.0, 0.0);
+        uint32_t pa = 0;
+        if (live) {
+            key_load_g<NW>(ak, (uint64_t)i, a);
+            ca = ac[i];
+            pa = ap[i];
+        } else {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) a[w] = 0;
+        }
         for (int c = 0; c < ncols; ++c) {
             uint64_t b[NW], o[NW];
             key_load_s<NW>(sk, (uint32_t)c, b);
             const uint32_t k = string_product<WP>(a, b, pa, sp[c], o);
-            const int64_t r = (j0 + c) * na + i;
-            key_store<NW>(ok, (uint64_t)r, o);
-            oc[r] = cmul(ca, sc[c]);
-            oph[r] = (uint8_t)k;
-            opb[r] = (uint8_t)normal_phase<WP>(o, k);
+            const int64_t r0 = (j0 + c) * na + i0;  // record of this warp's first row
+            // keys: staged per warp, then written as contiguous 16-byte pieces
+#pragma unroll
+            for (int w = 0; w < NW; ++w) ws[lane * KS + w] = o[w];
+            __syncwarp();
+            uint64_t* dst = ok + (uint64_t)r0 * NW;
+            for (uint32_t q = lane; q < nrow * (NW / 2); q += 32u) {
+                const uint32_t row = (2u * q) / NW, wd = (2u * q) % NW;
+                reinterpret_cast<ulonglong2*>(dst)[q] = make_ulonglong2(ws[row * KS + wd], ws[row * KS + wd + 1]);
+            }
+            __syncwarp();
+            if (live) {
+                const int64_t r = r0 + lane;
+                oc[r] = cmul(ca, sc[c]);
+                oph[r] = (uint8_t)k;
+                opb[r] = (uint8_t)normal_phase<WP>(o, k);
+            }
         }
     }
 }

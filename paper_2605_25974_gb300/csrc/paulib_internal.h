@@ -71,7 +71,7 @@ int padded_words(int W);
 
 // Pipeline tuning (paulib_set_tuning); never changes results.
 struct Tuning {
-    int coarse_factor = 16;
+    int coarse_factor = 32;
     int oversample = 32;
     int count_ctas_per_sm = 4;
     int range_ctas_per_sm = 2;

@@ -537,22 +537,159 @@ __global__ void __launch_bounds__(1024) k_select(const uint64_t* __restrict__ dk
 
 // ---------------------------------------------------------------- level 1: count
 
+// 64 bits of a register key starting at bit position P (word 0's top bit is
+// position 0); zero beyond the key.
+template <int NW>
+__device__ __forceinline__ uint64_t reg_bits64(const uint64_t (&k)[NW], uint32_t P) {
+    const uint32_t w = P >> 6, sh = P & 63u;
+    uint64_t v = 0, nx = 0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        if ((uint32_t)q == w) v = k[q];
+        if ((uint32_t)q == w + 1) nx = k[q];
+    }
+    return sh ? (v << sh) | (nx >> (64u - sh)) : v;
+}
+
+// Compares bits [0, P) of a register key with those of word-major key 0.
+template <int NW>
+__device__ __forceinline__ int prefix_cmp(const uint64_t (&k)[NW], const uint64_t* s, uint32_t stride, uint32_t P) {
+    int pc = 0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        if (pc == 0 && 64u * q < P) {
+            uint64_t a = k[q], b = s[(size_t)q * stride];
+            const uint32_t nb = P - 64u * q;
+            if (nb < 64u) {
+                const uint64_t m = ~0ull << (64u - nb);
+                a &= m;
+                b &= m;
+            }
+            if (a != b) pc = a < b ? -1 : 1;
+        }
+    }
+    return pc;
+}
+
 constexpr int kCountThreads = 256;
 constexpr int kCountCols = 64;
+
+// Coarse splitters are located through a 128-bit window of their keys: all
+// splitters share their first L bits (L is the first position where one of
+// them differs from splitter 0), and code1/code2 are key bits [L, L+64) and
+// [L+64, L+128).  A key whose first L bits differ from the shared prefix lies
+// below or above every splitter; other keys compare by the window, and by the
+// whole key (from the splitter table in global memory) only when the windows
+// are equal.  The search then reads 16 bytes of shared memory per step
+// instead of whole keys.
+template <int NW>
+__global__ void __launch_bounds__(1024) k_spl_codes(const uint64_t* __restrict__ spl, uint32_t nsp,
+                                                    uint64_t* codes, uint32_t* meta) {
+    __shared__ unsigned long long s_or[NW];
+    __shared__ uint32_t s_L;
+    for (int w = threadIdx.x; w < NW; w += blockDim.x) s_or[w] = 0ull;
+    __syncthreads();
+    uint64_t acc[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) acc[w] = 0;
+    for (uint32_t t = threadIdx.x; t < nsp; t += blockDim.x) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) acc[w] |= spl[(size_t)t * NW + w] ^ spl[w];
+    }
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        uint64_t v = acc[w];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicOr(&s_or[w], (unsigned long long)v);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t L = 64u * NW;
+        for (int w = 0; w < NW; ++w)
+            if (s_or[w]) { L = 64u * w + (uint32_t)__clzll((long long)s_or[w]); break; }
+        s_L = L;
+        meta[0] = L;
+    }
+    __syncthreads();
+    const uint32_t L = s_L;
+    for (uint32_t t = threadIdx.x; t < nsp; t += blockDim.x) {
+        uint64_t k[NW];
+        key_load_g<NW>(spl, t, k);
+        codes[t] = reg_bits64<NW>(k, L);
+        codes[nsp + t] = reg_bits64<NW>(k, L + 64u);
+    }
+}
+
+// Number of splitters <= k (see k_spl_codes); p0 is splitter 0 (shared).
+template <int NW>
+__device__ __forceinline__ uint32_t locate_coarse(const uint64_t (&k)[NW], const uint64_t* s_c1,
+                                                  const uint64_t* s_c2, const uint64_t* p0, uint32_t nsp,
+                                                  uint32_t L, const uint64_t* __restrict__ spl) {
+    // first L bits against the splitters' shared prefix
+    int pc = 0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        if (pc == 0 && 64u * q < L) {
+            uint64_t a = k[q], b = p0[q];
+            const uint32_t nb = L - 64u * q;
+            if (nb < 64u) {
+                const uint64_t m = ~0ull << (64u - nb);
+                a &= m;
+                b &= m;
+            }
+            if (a != b) pc = a < b ? -1 : 1;
+        }
+    }
+    if (pc) return pc < 0 ? 0u : nsp;
+    const uint64_t c1 = reg_bits64<NW>(k, L), c2 = reg_bits64<NW>(k, L + 64u);
+    uint32_t lo = 0, len = nsp;
+    while (len > 0) {
+        const uint32_t half = len >> 1, mid = lo + half;
+        const uint64_t s1 = s_c1[mid];
+        bool ge;
+        if (c1 != s1) {
+            ge = c1 > s1;
+        } else {
+            const uint64_t s2 = s_c2[mid];
+            ge = c2 != s2 ? c2 > s2 : key_cmp_m<NW>(k, spl + (size_t)mid * NW) >= 0;
+        }
+        if (ge) {
+            lo = mid + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo;
+}
+
+// Shared-memory layout of the counting kernels: codes [2][nsp], splitter 0,
+// then (products) one tile of right-hand keys, then the bucket histogram.
+template <int NW>
+__host__ __device__ constexpr size_t count_smem(uint32_t nsp, bool tile) {
+    return (size_t)nsp * 16 + (size_t)NW * 8 + (tile ? (size_t)kCountCols * NW * 8 : 0) + (size_t)(nsp + 1) * 4;
+}
 
 // Products: a tile is kCountThreads left terms x kCountCols right terms.
 template <int WP, int MODE>
 __global__ void __launch_bounds__(kCountThreads) k_count_prod(ProdSrc<WP, MODE> src, uint32_t nb_terms,
                                                                const uint64_t* __restrict__ spl,
+                                                               const uint64_t* __restrict__ codes,
+                                                               const uint32_t* __restrict__ meta,
                                                                uint32_t nsp, uint16_t* ids,
                                                                uint32_t* counts) {
     constexpr int NW = 2 * WP;
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* s_spl = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* s_b = s_spl + (size_t)nsp * NW;
+    uint64_t* s_c1 = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* s_c2 = s_c1 + nsp;
+    uint64_t* s_p0 = s_c2 + nsp;
+    uint64_t* s_b = s_p0 + NW;
     uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_b + kCountCols * NW);
     const uint32_t nbk = nsp + 1;
-    for (uint32_t q = threadIdx.x; q < nsp * NW; q += blockDim.x) s_spl[(q % NW) * nsp + q / NW] = spl[q];
+    const uint32_t L = meta[0];
+    for (uint32_t q = threadIdx.x; q < 2 * nsp; q += blockDim.x) s_c1[q] = codes[q];
+    for (uint32_t q = threadIdx.x; q < (uint32_t)NW; q += blockDim.x) s_p0[q] = spl[q];
     for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x) s_hist[q] = 0;
     const uint32_t na = src.na;
     const uint32_t ti_n = (na + kCountThreads - 1) / kCountThreads;
@@ -575,7 +712,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count_prod(ProdSrc<WP, MODE> 
                 const uint64_t* bb = s_b + c * NW;
 #pragma unroll
                 for (int q = 0; q < NW; ++q) k[q] = a[q] ^ bb[q];
-                const uint32_t bkt = upper_bound_skeys<NW>(s_spl, nsp, nsp, k);
+                const uint32_t bkt = locate_coarse<NW>(k, s_c1, s_c2, s_p0, nsp, L, spl);
                 ids[(uint64_t)(j0 + c) * na + i] = (uint16_t)bkt;
                 atomicAdd(&s_hist[bkt], 1u);
             }
@@ -589,20 +726,26 @@ __global__ void __launch_bounds__(kCountThreads) k_count_prod(ProdSrc<WP, MODE> 
 template <class Src>
 __global__ void __launch_bounds__(kCountThreads) k_count_lin(Src src, uint32_t R,
                                                               const uint64_t* __restrict__ spl,
+                                                              const uint64_t* __restrict__ codes,
+                                                              const uint32_t* __restrict__ meta,
                                                               uint32_t nsp, uint16_t* ids,
                                                               uint32_t* counts) {
     constexpr int NW = Src::NW;
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* s_spl = reinterpret_cast<uint64_t*>(smem);
-    uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_spl + (size_t)nsp * NW);
+    uint64_t* s_c1 = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* s_c2 = s_c1 + nsp;
+    uint64_t* s_p0 = s_c2 + nsp;
+    uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_p0 + NW);
     const uint32_t nbk = nsp + 1;
-    for (uint32_t q = threadIdx.x; q < nsp * NW; q += blockDim.x) s_spl[(q % NW) * nsp + q / NW] = spl[q];
+    const uint32_t L = meta[0];
+    for (uint32_t q = threadIdx.x; q < 2 * nsp; q += blockDim.x) s_c1[q] = codes[q];
+    for (uint32_t q = threadIdx.x; q < (uint32_t)NW; q += blockDim.x) s_p0[q] = spl[q];
     for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x) s_hist[q] = 0;
     __syncthreads();
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
         uint64_t k[NW];
         src.key(r, k);
-        const uint32_t bkt = upper_bound_skeys<NW>(s_spl, nsp, nsp, k);
+        const uint32_t bkt = locate_coarse<NW>(k, s_c1, s_c2, s_p0, nsp, L, spl);
         ids[r] = (uint16_t)bkt;
         atomicAdd(&s_hist[bkt], 1u);
     }
@@ -1555,38 +1698,6 @@ __global__ void __launch_bounds__(kWarpLeafWarps * 32) k_leaf_warp(Src src, L2Bu
     }
 }
 
-// 64 bits of a register key starting at bit position P (word 0's top bit is
-// position 0); zero beyond the key.
-template <int NW>
-__device__ __forceinline__ uint64_t reg_bits64(const uint64_t (&k)[NW], uint32_t P) {
-    const uint32_t w = P >> 6, sh = P & 63u;
-    uint64_t v = 0, nx = 0;
-#pragma unroll
-    for (int q = 0; q < NW; ++q) {
-        if ((uint32_t)q == w) v = k[q];
-        if ((uint32_t)q == w + 1) nx = k[q];
-    }
-    return sh ? (v << sh) | (nx >> (64u - sh)) : v;
-}
-
-// Compares bits [0, P) of a register key with those of word-major key 0.
-template <int NW>
-__device__ __forceinline__ int prefix_cmp(const uint64_t (&k)[NW], const uint64_t* s, uint32_t stride, uint32_t P) {
-#pragma unroll
-    for (int q = 0; q < NW; ++q) {
-        if (64u * q >= P) break;
-        uint64_t a = k[q], b = s[(size_t)q * stride];
-        const uint32_t nb = P - 64u * q;
-        if (nb < 64u) {
-            const uint64_t m = ~0ull << (64u - nb);
-            a &= m;
-            b &= m;
-        }
-        if (a != b) return a < b ? -1 : 1;
-    }
-    return 0;
-}
-
 // ---- routing: a range that needs no split at this point goes to the leaf
 // lists (or is emitted at once when it holds one record); a range to split,
 // or one whose keys are all equal, goes on the CTA's stack.  Called by all
@@ -2156,24 +2267,29 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
         check_cuda(cudaMemsetAsync(cnt_s.p, 0, (size_t)nbk * 4, st), "memset");
         {
         StageScope ssc(ST_COUNT, st);
+        Scratch codes((size_t)nsp * 16, st), meta(16, st);
+        k_spl_codes<NW><<<1, 1024, 0, st>>>(spl.as<uint64_t>(), nsp, codes.as<uint64_t>(), meta.as<uint32_t>());
+        note_launch(ST_COUNT);
         if constexpr (IsProd<Src>::value) {
-            const size_t sm = (size_t)nsp * NW * 8 + (size_t)kCountCols * NW * 8 + (size_t)nbk * 4;
+            const size_t sm = count_smem<NW>(nsp, true);
             auto kern = k_count_prod<WP, MODE>;
             smem_attr(kern, sm);
             const uint64_t tiles = (uint64_t)((src.na + kCountThreads - 1) / kCountThreads) *
                                    ((nb_terms + kCountCols - 1) / kCountCols);
             const unsigned grid = (unsigned)std::max<uint64_t>(
                 1, std::min<uint64_t>(tiles, (uint64_t)sms * (uint64_t)tune.count_ctas_per_sm));
-            kern<<<grid, kCountThreads, sm, st>>>(src, nb_terms, spl.as<uint64_t>(), nsp, subid.as<uint16_t>(),
+            kern<<<grid, kCountThreads, sm, st>>>(src, nb_terms, spl.as<uint64_t>(), codes.as<uint64_t>(),
+                                                 meta.as<uint32_t>(), nsp, subid.as<uint16_t>(),
                                                  cnt_s.as<uint32_t>());
         } else {
-            const size_t sm = (size_t)nsp * NW * 8 + (size_t)nbk * 4;
+            const size_t sm = count_smem<NW>(nsp, false);
             auto kern = k_count_lin<Src>;
             smem_attr(kern, sm);
             const unsigned grid = (unsigned)std::max<uint64_t>(
                 1, std::min<uint64_t>(((uint64_t)R + kCountThreads - 1) / kCountThreads,
                                       (uint64_t)sms * (uint64_t)tune.count_ctas_per_sm));
-            kern<<<grid, kCountThreads, sm, st>>>(src, R, spl.as<uint64_t>(), nsp, subid.as<uint16_t>(),
+            kern<<<grid, kCountThreads, sm, st>>>(src, R, spl.as<uint64_t>(), codes.as<uint64_t>(),
+                                                 meta.as<uint32_t>(), nsp, subid.as<uint16_t>(),
                                                  cnt_s.as<uint32_t>());
         }
         note_launch(ST_COUNT);
