@@ -30,10 +30,14 @@ HBM_PEAK_FALLBACK = 6800.0
 # FP64 peak derived from unit counts: 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 
-# DRAM bytes (read + write) per product of a stage's kernels, from ncu
-# counters on the n=200, 6,000-term case scaled by product count; keyed by
-# (stage, n_qubits).  Set to None when the kernels change.
-TRAFFIC_PER_PRODUCT = {}
+# DRAM bytes (read + write) per product of a stage's kernels in one timed
+# step, from ncu counters (dram__bytes_read.sum + dram__bytes_write.sum) on
+# the 30,000-term n=200 workload (summarised under profiles/); keyed by
+# (stage, n_qubits).  Entries must be removed when those kernels change.
+TRAFFIC_PER_PRODUCT = {
+    ("leaf", 200): 42.96e9 / 9e8,    # k_leaf_warp + k_leaf_block
+    ("level2", 200): 25.03e9 / 9e8,  # k_level2
+}
 
 WORKLOADS = {
     "jw_hh_n200_m30000": dict(n=200, m=30000, seed=401),
@@ -285,6 +289,8 @@ def run_ours(args):
         dist.init_process_group("nccl")
     from paper_2605_25974_gb300 import paulib
     paulib.load()
+    if args.coarse_factor > 0:
+        paulib.set_tuning(0, args.coarse_factor, 0, 0, 0)
 
     h = make_workload(args.workload)
     products = h.m * h.m
@@ -499,6 +505,9 @@ def main():
     ap.add_argument("--workload", default="jw_hh_n200_m30000", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-products leg")
+    ap.add_argument("--coarse-factor", type=int, default=0,
+                    help="first-level fan-out of the canonicalisation (0: library default); for profiling "
+                         "small cases with the range mix of large ones")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
