@@ -105,6 +105,91 @@ void dev_free(void* p, cudaStream_t s) {
     cudaFreeAsync(p, s);
 }
 
+// ---- scratch cache (see paulib_internal.h)
+namespace {
+struct CachedBlock {
+    void* p;
+    size_t bytes;
+    int dev;
+    cudaStream_t s;
+};
+std::mutex g_cache_mu;
+std::vector<CachedBlock> g_cache;
+constexpr size_t kCacheMin = (size_t)1 << 20;
+constexpr size_t kCacheMaxBlocks = 64;
+}  // namespace
+
+void* scratch_alloc(size_t bytes, cudaStream_t s) {
+    if (bytes < kCacheMin || g_arena.mode != 0 || g_alloc) return dev_alloc(bytes, s);
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        size_t best = g_cache.size();
+        for (size_t i = 0; i < g_cache.size(); ++i) {
+            const CachedBlock& b = g_cache[i];
+            if (b.dev != dev || b.s != s || b.bytes < bytes || b.bytes > bytes + bytes / 4) continue;
+            if (best == g_cache.size() || b.bytes < g_cache[best].bytes) best = i;
+        }
+        if (best != g_cache.size()) {
+            void* p = g_cache[best].p;
+            g_cache[best] = g_cache.back();
+            g_cache.pop_back();
+            return p;
+        }
+    }
+    try {
+        return dev_alloc(bytes, s);
+    } catch (const Error& e) {
+        if (e.status != PAULIB_ERR_OOM) throw;
+        scratch_cache_flush();  // give the cached blocks back and try once more
+        return dev_alloc(bytes, s);
+    }
+}
+
+void scratch_free(void* p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    if (bytes < kCacheMin || g_arena.mode != 0 || g_free) {
+        dev_free(p, s);
+        return;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev_free(p, s);
+        return;
+    }
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_cache.push_back(CachedBlock{p, bytes, dev, s});
+    if (g_cache.size() > kCacheMaxBlocks) {  // bounded: the oldest block goes back to the pool
+        const CachedBlock old = g_cache.front();
+        g_cache.erase(g_cache.begin());
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(old.dev);
+        cudaFreeAsync(old.p, old.s);
+        cudaSetDevice(cur);
+        cudaGetLastError();
+    }
+}
+
+void scratch_cache_flush() {
+    std::vector<CachedBlock> blocks;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        blocks.swap(g_cache);
+    }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (const CachedBlock& b : blocks) {
+        cudaSetDevice(b.dev);
+        cudaFreeAsync(b.p, b.s);
+    }
+    cudaSetDevice(cur);
+    cudaDeviceSynchronize();  // the frees must complete before the pool can reuse the memory
+    cudaGetLastError();
+}
+
 int padded_words(int W) {
     int wp = 1;
     while (wp < W) wp *= 2;

@@ -49,21 +49,33 @@ void arena_replay_begin(void* base, size_t bytes);
 void arena_replay_end();
 bool capture_safe();
 
+// Pipeline scratch.  Blocks of 1 MiB or more are kept by the library after
+// use and handed to later requests of (about) the same size on the same
+// stream and device; the stream order makes the reuse safe without events.
+// This keeps the device pool's cached memory for the outputs, whose sizes
+// repeat from call to call, instead of letting the large scratch requests
+// carve it up (which made every large output map fresh memory).  Other
+// blocks, arena replays and user allocators go straight to dev_alloc.
+void* scratch_alloc(size_t bytes, cudaStream_t s);
+void scratch_free(void* p, size_t bytes, cudaStream_t s);
+void scratch_cache_flush();
+
 // A scratch buffer freed (stream ordered) when it goes out of scope.
 struct Scratch {
     void* p = nullptr;
     cudaStream_t s = nullptr;
+    size_t bytes = 0;
     Scratch() = default;
-    Scratch(size_t bytes, cudaStream_t st) : p(bytes ? dev_alloc(bytes, st) : nullptr), s(st) {}
+    Scratch(size_t n, cudaStream_t st) : p(n ? scratch_alloc(n, st) : nullptr), s(st), bytes(n) {}
     Scratch(const Scratch&) = delete;
     Scratch& operator=(const Scratch&) = delete;
-    Scratch(Scratch&& o) noexcept : p(o.p), s(o.s) { o.p = nullptr; }
+    Scratch(Scratch&& o) noexcept : p(o.p), s(o.s), bytes(o.bytes) { o.p = nullptr; }
     Scratch& operator=(Scratch&& o) noexcept {
-        if (this != &o) { release(); p = o.p; s = o.s; o.p = nullptr; }
+        if (this != &o) { release(); p = o.p; s = o.s; bytes = o.bytes; o.p = nullptr; }
         return *this;
     }
     ~Scratch() { release(); }
-    void release() { if (p) dev_free(p, s); p = nullptr; }
+    void release() { if (p) scratch_free(p, bytes, s); p = nullptr; }
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
