@@ -802,35 +802,93 @@ static __global__ void __launch_bounds__(1024) k_scan_u64(const uint64_t* __rest
 // ---------------------------------------------------------------- level 1: scatter
 
 constexpr int kScatterThreads = 512;
-constexpr uint32_t kScatterChunk = 32768;
+constexpr uint32_t kScatterChunk = 16384;
 
+// Reads the bucket ids of records r0 .. r0+7 (one 16-byte load when all
+// eight are in range; r0 is a multiple of 8, so the load is aligned).
+__device__ __forceinline__ void load_ids8(const uint16_t* __restrict__ ids, uint32_t r0, uint32_t end,
+                                          uint32_t (&b)[8]) {
+    if (r0 + 8u <= end) {
+        const uint4 v = *reinterpret_cast<const uint4*>(ids + r0);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            b[2 * q] = w[q] & 0xffffu;
+            b[2 * q + 1] = w[q] >> 16;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) b[q] = r0 + q < end ? ids[r0 + q] : 0u;
+    }
+}
+
+// Scatter of records into their coarse ranges, one chunk of kScatterChunk
+// records at a time: count per range, take each range's global slots with one
+// atomic per (chunk, range), order the chunk's records by range in shared
+// memory (a counting sort), then write each range's run contiguously so that
+// the stores coalesce instead of landing 4 bytes at a time.
 static __global__ void __launch_bounds__(kScatterThreads) k_scatter(const uint16_t* __restrict__ ids, uint32_t R,
                                                              uint32_t nbk, uint64_t* cursor,
                                                              uint32_t* rec, uint32_t sym_na) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);
-    uint64_t* s_base = reinterpret_cast<uint64_t*>(s_cnt + ((nbk + 1) & ~1u));
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);                       // [nbk] counts, then cursors
+    uint32_t* s_off = s_cnt + ((nbk + 1) & ~1u);                               // [nbk + 1] chunk-local offsets
+    uint64_t* s_base = reinterpret_cast<uint64_t*>(s_off + ((nbk + 2) & ~1u)); // [nbk] global first slot
+    uint32_t* s_rec = reinterpret_cast<uint32_t*>(s_base + nbk);               // [kScatterChunk] records by range
+    uint16_t* s_bid = reinterpret_cast<uint16_t*>(s_rec + kScatterChunk);      // [kScatterChunk] their ranges
+    __shared__ uint32_t s_warp[32];
+    // a symmetric product has no record for i > j (r = j*na + i)
+    auto live = [&](uint32_t r) { return !sym_na || r % sym_na <= r / sym_na; };
     for (uint64_t c0 = (uint64_t)blockIdx.x * kScatterChunk; c0 < R; c0 += (uint64_t)gridDim.x * kScatterChunk) {
         const uint32_t c1 = (uint32_t)mn<uint64_t>(R, c0 + kScatterChunk);
         __syncthreads();
         for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x) s_cnt[q] = 0;
         __syncthreads();
-        for (uint32_t r = (uint32_t)c0 + threadIdx.x; r < c1; r += blockDim.x) {
-            if (sym_na && r % sym_na > r / sym_na) continue;  // no record for i > j
-            atomicAdd(&s_cnt[ids[r]], 1u);
+        for (uint32_t r0 = (uint32_t)c0 + 8u * threadIdx.x; r0 < c1; r0 += 8u * blockDim.x) {
+            uint32_t b[8];
+            load_ids8(ids, r0, c1, b);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (r0 + q < c1 && live(r0 + q)) atomicAdd(&s_cnt[b[q]], 1u);
         }
         __syncthreads();
-        for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x) {
-            const uint32_t c = s_cnt[q];
-            s_base[q] = c ? atomicAdd(reinterpret_cast<unsigned long long*>(cursor + q), (unsigned long long)c) : 0ull;
-            s_cnt[q] = 0;
+        // chunk-local exclusive offsets of the ranges (block scan in slices)
+        {
+            const uint32_t per = (nbk + kScatterThreads - 1) / kScatterThreads;
+            const uint32_t q0 = threadIdx.x * per;
+            uint32_t loc = 0;
+            for (uint32_t q = q0; q < q0 + per && q < nbk; ++q) loc += s_cnt[q];
+            uint32_t tot;
+            uint32_t ex = block_excl_scan<kScatterThreads>(loc, s_warp, tot);
+            for (uint32_t q = q0; q < q0 + per && q < nbk; ++q) {
+                const uint32_t c = s_cnt[q];
+                s_off[q] = ex;
+                s_base[q] = c ? atomicAdd(reinterpret_cast<unsigned long long*>(cursor + q), (unsigned long long)c)
+                              : 0ull;
+                s_cnt[q] = ex;  // becomes the placement cursor
+                ex += c;
+            }
+            if (threadIdx.x == 0) s_off[nbk] = tot;
         }
         __syncthreads();
-        for (uint32_t r = (uint32_t)c0 + threadIdx.x; r < c1; r += blockDim.x) {
-            if (sym_na && r % sym_na > r / sym_na) continue;
-            const uint32_t b = ids[r];
-            const uint32_t p = atomicAdd(&s_cnt[b], 1u);
-            rec[s_base[b] + p] = r;
+        for (uint32_t r0 = (uint32_t)c0 + 8u * threadIdx.x; r0 < c1; r0 += 8u * blockDim.x) {
+            uint32_t b[8];
+            load_ids8(ids, r0, c1, b);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const uint32_t r = r0 + q;
+                if (r < c1 && live(r)) {
+                    const uint32_t p = atomicAdd(&s_cnt[b[q]], 1u);
+                    s_rec[p] = r;
+                    s_bid[p] = (uint16_t)b[q];
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t nloc = s_off[nbk];
+        for (uint32_t p = threadIdx.x; p < nloc; p += blockDim.x) {
+            const uint32_t b = s_bid[p];
+            rec[s_base[b] + (p - s_off[b])] = s_rec[p];
         }
     }
 }
@@ -2301,10 +2359,12 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
         note_launch(ST_SCATTER);
         Scratch cursor((size_t)nbk * 8, st);
         check_cuda(cudaMemcpyAsync(cursor.p, boff_s.p, (size_t)nbk * 8, cudaMemcpyDeviceToDevice, st), "cursor");
-        const size_t sm = (size_t)((nbk + 1) & ~1u) * 4 + (size_t)nbk * 8;
+        const size_t sm = (size_t)((nbk + 1) & ~1u) * 4 + (size_t)((nbk + 2) & ~1u) * 4 + (size_t)nbk * 8 +
+                          (size_t)kScatterChunk * 6;
         smem_attr(k_scatter, sm);
+        const uint64_t per_sm = std::max<uint64_t>(1, (220u * 1024u) / (sm + 1024u));
         const unsigned grid = (unsigned)std::max<uint64_t>(
-            1, std::min<uint64_t>(((uint64_t)R + kScatterChunk - 1) / kScatterChunk, (uint64_t)sms * 2));
+            1, std::min<uint64_t>(((uint64_t)R + kScatterChunk - 1) / kScatterChunk, (uint64_t)sms * per_sm));
         k_scatter<<<grid, kScatterThreads, sm, st>>>(subid.as<uint16_t>(), R, nbk, cursor.as<uint64_t>(),
                                                     recA.as<uint32_t>(), sym_na);
         note_launch(ST_SCATTER);
