@@ -544,9 +544,9 @@ __device__ __forceinline__ uint64_t reg_bits64(const uint64_t (&k)[NW], uint32_t
     const uint32_t w = P >> 6, sh = P & 63u;
     uint64_t v = 0, nx = 0;
 #pragma unroll
-    for (int q = 0; q < NW; ++q) {
-        if ((uint32_t)q == w) v = k[q];
-        if ((uint32_t)q == w + 1) nx = k[q];
+    for (int q = 0; q < NW; ++q) {  // masks rather than an index, so k stays in registers
+        v |= k[q] & (0ull - (uint64_t)((uint32_t)q == w));
+        nx |= k[q] & (0ull - (uint64_t)((uint32_t)q == w + 1u));
     }
     return sh ? (v << sh) | (nx >> (64u - sh)) : v;
 }
