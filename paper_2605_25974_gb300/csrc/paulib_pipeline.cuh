@@ -1436,16 +1436,77 @@ __device__ __forceinline__ uint32_t warp_run_sums(const typename Src::V (&vr)[EP
                                                   const bool (&hd)[EPL], Acc<MODE> (&acc)[EPL], uint32_t lane,
                                                   uint32_t n, uint32_t lo, const uint64_t* wk, uint16_t* repl,
                                                   uint64_t* Tkeys, double2* Tcoef, uint8_t* oflag) {
+    using V = typename Src::V;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    V vv[EPL];
+    bool cont[EPL];  // position continues a run
+#pragma unroll
+    for (uint32_t e = 0; e < EPL; ++e) {
+        vv[e] = fetch_v<V, EPL>(vr, x[e].s);
+        cont[e] = e * 32u + lane < n && !hd[e];
+    }
+    // Fast path: every run holds one or two records (each string of H*H
+    // typically arises from P_aP_b and P_bP_a), so a run's total is its last
+    // value plus, for a two-record run, the value before it.
+    bool longer = false;
+#pragma unroll
+    for (uint32_t e = 0; e < EPL; ++e) {
+        bool pc = __shfl_up_sync(0xffffffffu, cont[e], 1);
+        const bool pc_row = __shfl_sync(0xffffffffu, cont[e > 0 ? e - 1 : 0], 31);
+        if (lane == 0) pc = e > 0 ? pc_row : false;
+        longer = longer || (cont[e] && pc);
+    }
+    if (!__any_sync(0xffffffffu, longer)) {
+        uint32_t heads = 0;
+#pragma unroll
+        for (uint32_t e = 0; e < EPL; ++e) {
+            const uint32_t g = e * 32u + lane;
+            const bool valid = g < n;
+            V pv;
+            pv.x = __shfl_up_sync(0xffffffffu, vv[e].x, 1);
+            pv.y = __shfl_up_sync(0xffffffffu, vv[e].y, 1);
+            const V& prow = vv[e > 0 ? e - 1 : 0];
+            const auto px = __shfl_sync(0xffffffffu, prow.x, 31);
+            const auto py = __shfl_sync(0xffffffffu, prow.y, 31);
+            if (lane == 0) {
+                pv.x = px;
+                pv.y = py;
+            }
+            Acc<MODE> a;
+            if (valid) {
+                if (!hd[e]) a.add(pv);  // record order: the run's first value, then its second
+                a.add(vv[e]);
+            }
+            const uint32_t hb = __ballot_sync(0xffffffffu, hd[e]);
+            const uint32_t oidx = heads + __popc(hb & lt_mask) + (hd[e] ? 1u : 0u) - 1u;
+            const bool nh_same = __shfl_down_sync(0xffffffffu, hd[e], 1);
+            const bool nh_next = __shfl_sync(0xffffffffu, hd[e + 1 < EPL ? e + 1 : e], 0);
+            const bool next_head = lane < 31 ? nh_same : (e + 1 < EPL ? nh_next : false);
+            const bool last = valid && (g + 1 >= n || next_head);
+            if (last) {
+                if constexpr (DIRECT) {
+                    uint64_t k[NW];
+                    skey_load<NW>(wk, WL, x[e].s, k);
+                    key_store<NW>(Tkeys, (uint64_t)lo + oidx, k);
+                    Tcoef[(uint64_t)lo + oidx] = a.result();
+                    oflag[(uint64_t)lo + oidx] = 1;
+                } else {
+                    repl[oidx] = (uint16_t)(x[e].s | (g << 8));
+                }
+            }
+            acc[e] = a;
+            heads += __popc(hb);
+        }
+        return heads;
+    }
     Acc<MODE> carry;
     uint32_t heads_before = 0;
-    const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
     for (uint32_t e = 0; e < EPL; ++e) {
         const uint32_t g = e * 32u + lane;
         const bool valid = g < n;
         Acc<MODE> a;
-        const typename Src::V v = fetch_v<typename Src::V, EPL>(vr, x[e].s);
-        if (valid) a.add(v);
+        if (valid) a.add(vv[e]);
         bool f = hd[e];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
