@@ -922,24 +922,27 @@ struct L2Cfg {
 // number, so the order is total and deterministic.  Slots >= n are padding
 // that sorts last.
 
+// w0: keys with equal codes agree on every word before w0 (the word holding
+// position L2 + 64), so whole-key comparisons start there.
 template <int NW, uint32_t CAP>
 __device__ __forceinline__ bool slot_gt(uint32_t a, uint32_t b, const uint64_t* c1s, const uint64_t* keys_s,
-                                        uint32_t n, const uint32_t* recs) {
+                                        uint32_t n, const uint32_t* recs, int w0) {
     if (a >= n || b >= n) return a >= n && (b < n || a > b);
     const uint64_t ca = c1s[a], cb = c1s[b];
     if (ca != cb) return ca > cb;
     const uint64_t da = c1s[CAP + a], db = c1s[CAP + b];
     if (da != db) return da > db;
-    const int c = skey_cmp<NW>(keys_s, CAP, a, b);
+    const int c = skey_cmp_from<NW>(keys_s, CAP, a, b, w0);
     if (c) return c > 0;
     if (recs) return recs[a] > recs[b];
     return a > b;
 }
 
 template <int NW, uint32_t CAP>
-__device__ __forceinline__ bool slot_key_neq(uint32_t a, uint32_t b, const uint64_t* c1s, const uint64_t* keys_s) {
+__device__ __forceinline__ bool slot_key_neq(uint32_t a, uint32_t b, const uint64_t* c1s, const uint64_t* keys_s,
+                                             int w0) {
     if (c1s[a] != c1s[b] || c1s[CAP + a] != c1s[CAP + b]) return true;
-    return skey_cmp<NW>(keys_s, CAP, a, b) != 0;
+    return skey_cmp_from<NW>(keys_s, CAP, a, b, w0) != 0;
 }
 
 // 64 bits of key t starting at bit position P (word 0's top bit is position 0).
@@ -1004,7 +1007,7 @@ __device__ void build_codes(uint64_t* c1s, const uint64_t* keys_s, uint32_t n, u
 // the sorted slots (ord or tmp).
 template <int NW, int T, uint32_t CAP>
 __device__ uint16_t* merge_sort_slots(uint16_t* ord, uint16_t* tmp, const uint64_t* c1s, const uint64_t* keys_s,
-                                      uint32_t n, uint32_t size, const uint32_t* recs) {
+                                      uint32_t n, uint32_t size, const uint32_t* recs, int w0) {
     constexpr uint32_t EMAX = CAP / (uint32_t)T >= 2u ? CAP / (uint32_t)T : 2u;
     const uint32_t em = size / (uint32_t)T >= 2u ? size / (uint32_t)T : 2u;
     const uint32_t nthr = size / em;
@@ -1015,7 +1018,7 @@ __device__ uint16_t* merge_sort_slots(uint16_t* ord, uint16_t* tmp, const uint64
             if (k < em) {
                 uint32_t x = t * em + k;
                 uint32_t q = k;
-                while (q > 0 && slot_gt<NW, CAP>(v[q - 1], x, c1s, keys_s, n, recs)) {
+                while (q > 0 && slot_gt<NW, CAP>(v[q - 1], x, c1s, keys_s, n, recs, w0)) {
                     v[q] = v[q - 1];
                     --q;
                 }
@@ -1039,7 +1042,7 @@ __device__ uint16_t* merge_sort_slots(uint16_t* ord, uint16_t* tmp, const uint64
             uint32_t lo = d > s ? d - s : 0u, hi = d < s ? d : s;
             while (lo < hi) {  // number of A elements among the first d outputs
                 const uint32_t mid = (lo + hi) >> 1;
-                if (slot_gt<NW, CAP>(A[mid], B[d - mid - 1], c1s, keys_s, n, recs)) hi = mid;
+                if (slot_gt<NW, CAP>(A[mid], B[d - mid - 1], c1s, keys_s, n, recs, w0)) hi = mid;
                 else lo = mid + 1;
             }
             uint32_t i = lo, j = d - lo;
@@ -1047,7 +1050,7 @@ __device__ uint16_t* merge_sort_slots(uint16_t* ord, uint16_t* tmp, const uint64
                 bool takeA;
                 if (i >= s) takeA = false;
                 else if (j >= s) takeA = true;
-                else takeA = !slot_gt<NW, CAP>(A[i], B[j], c1s, keys_s, n, recs);
+                else takeA = !slot_gt<NW, CAP>(A[i], B[j], c1s, keys_s, n, recs, w0);
                 dst[o + k] = takeA ? A[i++] : B[j++];
             }
         }
@@ -1133,12 +1136,13 @@ __device__ __forceinline__ Acc<MODE> block_seg_carry(bool flag, const Acc<MODE>&
 
 // Key order of two slots (codes, then full keys); records are ignored.
 template <int NW, uint32_t CAP>
-__device__ __forceinline__ int slot_key_cmp(uint32_t a, uint32_t b, const uint64_t* c1s, const uint64_t* keys_s) {
+__device__ __forceinline__ int slot_key_cmp(uint32_t a, uint32_t b, const uint64_t* c1s, const uint64_t* keys_s,
+                                            int w0) {
     const uint64_t ca = c1s[a], cb = c1s[b];
     if (ca != cb) return ca < cb ? -1 : 1;
     const uint64_t da = c1s[CAP + a], db = c1s[CAP + b];
     if (da != db) return da < db ? -1 : 1;
-    return skey_cmp<NW>(keys_s, CAP, a, b);
+    return skey_cmp_from<NW>(keys_s, CAP, a, b, w0);
 }
 
 // Block-wide scratch of the range and leaf kernels.
@@ -1200,7 +1204,8 @@ __device__ void block_leaf(const Src& src, const uint32_t* cur, uint32_t lo, uin
     while (size < n) size <<= 1;
     __syncthreads();
     build_codes<NW, T, CAP>(c1s, keys_s, n, sh.orr, sh.L);
-    const uint16_t* srt = merge_sort_slots<NW, T, CAP>(ord_s, tmp_s, c1s, keys_s, n, size, rec_s);
+    const int w0 = (int)((sh.L[1] + 64u) >> 6);
+    const uint16_t* srt = merge_sort_slots<NW, T, CAP>(ord_s, tmp_s, c1s, keys_s, n, size, rec_s, w0);
     const uint32_t p0 = (uint32_t)tid * PP;
     bool hd[PP];
     V v[PP];
@@ -1213,7 +1218,7 @@ __device__ void block_leaf(const Src& src, const uint32_t* cur, uint32_t lo, uin
         if (act && p < n) {
             sl[q] = srt[p];
             v[q] = src.coefv(rec_s[sl[q]], ph_s[sl[q]]);
-            hd[q] = (p == 0) || slot_key_neq<NW, CAP>(sl[q], srt[p - 1], c1s, keys_s);
+            hd[q] = (p == 0) || slot_key_neq<NW, CAP>(sl[q], srt[p - 1], c1s, keys_s, w0);
             nh += hd[q] ? 1u : 0u;
         }
     }
@@ -1241,7 +1246,7 @@ __device__ void block_leaf(const Src& src, const uint32_t* cur, uint32_t lo, uin
             bool last = p + 1 >= n;
             if (!last) {
                 if (q + 1 < PP) last = hd[q + 1];
-                else last = slot_key_neq<NW, CAP>(srt[p + 1], sl[q], c1s, keys_s);
+                else last = slot_key_neq<NW, CAP>(srt[p + 1], sl[q], c1s, keys_s, w0);
             }
             if (last) {
                 uint64_t k[NW];
@@ -1974,7 +1979,8 @@ __global__ void __launch_bounds__(kL2Threads, 2) k_level2(Src src, uint32_t nbk,
             }
             __syncthreads();
             build_codes<NW, T, CAP>(c1s, keys_s, S, sh.orr, sh.L);
-            const uint16_t* srt = merge_sort_slots<NW, T, CAP>(ord_s, tmp_s, c1s, keys_s, S, S, nullptr);
+            const int w0 = (int)((sh.L[1] + 64u) >> 6);
+            const uint16_t* srt = merge_sort_slots<NW, T, CAP>(ord_s, tmp_s, c1s, keys_s, S, S, nullptr, w0);
             // Candidate t (1 <= t < want) is the key at sample rank t*S/want.
             // A candidate equal to the one before it adds nothing; a key whose
             // run in the sample covers half a target range or more is heavy and
@@ -1989,18 +1995,18 @@ __global__ void __launch_bounds__(kL2Threads, 2) k_level2(Src src, uint32_t nbk,
                     const uint32_t rho = (uint32_t)(((uint64_t)t * S) / want);
                     const uint32_t ci = srt[rho];
                     const uint32_t rp = (uint32_t)(((uint64_t)(t - 1) * S) / want);
-                    if (t == 1 || slot_key_cmp<NW, CAP>(srt[rp], ci, c1s, keys_s) != 0) {
+                    if (t == 1 || slot_key_cmp<NW, CAP>(srt[rp], ci, c1s, keys_s, w0) != 0) {
                         skey_load<NW>(keys_s, CAP, ci, k);
                         uint32_t a0 = 0, a1 = rho;  // first sample rank holding this key
                         while (a0 < a1) {
                             const uint32_t mid = (a0 + a1) >> 1;
-                            if (slot_key_cmp<NW, CAP>(srt[mid], ci, c1s, keys_s) < 0) a0 = mid + 1;
+                            if (slot_key_cmp<NW, CAP>(srt[mid], ci, c1s, keys_s, w0) < 0) a0 = mid + 1;
                             else a1 = mid;
                         }
                         uint32_t b0 = rho, b1 = S - 1;  // last sample rank holding it
                         while (b0 < b1) {
                             const uint32_t mid = (b0 + b1 + 1) >> 1;
-                            if (slot_key_cmp<NW, CAP>(srt[mid], ci, c1s, keys_s) > 0) b1 = mid - 1;
+                            if (slot_key_cmp<NW, CAP>(srt[mid], ci, c1s, keys_s, w0) > 0) b1 = mid - 1;
                             else b0 = mid;
                         }
                         heavy = b0 - a0 + 1 >= heavy_min;
