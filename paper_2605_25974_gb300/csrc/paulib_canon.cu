@@ -173,7 +173,7 @@ static void noalloc_run(int32_t n_qubits, int64_t na_, const uint64_t* a_x, cons
         k_na_convert<WP><<<(unsigned)((nb_ + 255) / 256), 256, 0, st>>>(
             nb_, W, n_qubits, b_x, b_z, reinterpret_cast<const double2*>(b_c), bk, bc, bp, err);
         k_iota<<<(R + 255) / 256, 256, 0, st>>>(recA, R, boff, bflags);
-        Src src{ak, bk, ap, bp, ac, bc, (uint32_t)na_};
+        Src src{ak, bk, ap, bp, ac, bc, (uint32_t)na_, 0u, recip64((uint32_t)na_)};
         L2Bufs lb{recA, recB, sub, ctr, stack, spl, tk, tc, oflag, lists, lists + na::kSmallCap,
                   (uint32_t)na::kSmallCap, (uint32_t)na::kMedCap, err};
         launch_level2<Src, M_FP64>(src, 1u, boff, bflags, lb, 1u, nch, ccount, coff, st);

@@ -73,8 +73,12 @@ struct ProdSrc {
     const V* bc;
     uint32_t na;
     uint32_t sym = 0;
+    uint64_t na_inv = 0;  // ceil(2^64 / na), or 0 when na = 1 (see recip64)
+    // j = r / na by one high multiply: exact for every 32-bit r, because the
+    // reciprocal's error adds less than 2^-32 while r / na's fractional part
+    // stays at least 1 / na > 2^-32 away from the next integer.
     __device__ __forceinline__ void split(uint32_t r, uint32_t& i, uint32_t& j) const {
-        j = r / na;
+        j = na_inv ? (uint32_t)__umul64hi((uint64_t)r, na_inv) : r;
         i = r - j * na;
     }
     __device__ __forceinline__ void key(uint32_t r, uint64_t (&k)[NW]) const {
@@ -135,6 +139,8 @@ struct ProdSrc {
         return apply(mul_v(ac[i], bc[j]), ph);
     }
 };
+
+inline uint64_t recip64(uint32_t d) { return d <= 1 ? 0ull : ~0ull / d + 1ull; }
 
 // Terms of one sum: record r is term r; value i^phase * c (or 1 when c is
 // null, which counts occurrences).
@@ -2522,7 +2528,8 @@ static paulib_sum* product_mode(const paulib_sum* a, const paulib_sum* b, cudaSt
         bc = fb.as<V>();
     }
     // the same sum on both sides: only i <= j pairs are generated
-    Src src{a->keys, b->keys, a->pbase, b->pbase, ac, bc, (uint32_t)a->n_terms, a == b ? 1u : 0u};
+    Src src{a->keys, b->keys, a->pbase, b->pbase, ac, bc, (uint32_t)a->n_terms, a == b ? 1u : 0u,
+            recip64((uint32_t)a->n_terms)};
     return finish<Src, MODE>(src, R, (uint32_t)b->n_terms, a->n_qubits, st);
 }
 
