@@ -35,8 +35,8 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 # the 30,000-term n=200 workload (summarised under profiles/); keyed by
 # (stage, n_qubits).  Entries must be removed when those kernels change.
 TRAFFIC_PER_PRODUCT = {
-    ("leaf", 200): 42.96e9 / 9e8,    # k_leaf_warp + k_leaf_block
-    ("level2", 200): 25.03e9 / 9e8,  # k_level2
+    ("leaf", 200): 42.80e9 / 9e8,    # k_leaf_warp + k_leaf_block
+    ("level2", 200): 24.27e9 / 9e8,  # k_level2
 }
 
 WORKLOADS = {
@@ -405,6 +405,7 @@ def run_ours(args):
         pm = statistics.mean(tms)
         precision[prec] = dict(ms_per_step=pm, value=products / (pm / 1e3), speedup_vs_fp64=ms / pm, **stats)
     del rx, rz, rc, dx, dz, dc, rmag
+    torch.cuda.empty_cache()  # the outer-product leg below needs the memory back
 
     # ---- end to end through the C ABI with host buffers
     hx = torch.from_numpy(h.x.view(np.int64)).pin_memory()

@@ -92,6 +92,18 @@ void* dev_alloc(size_t bytes, cudaStream_t s) {
     configure_pool_once();
     void* p = nullptr;
     cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e == cudaErrorMemoryAllocation) {
+        // give back the cached scratch blocks and the pool's unused memory, then try once more
+        cudaGetLastError();
+        scratch_cache_flush();
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
+            cudaMemPoolTrimTo(pool, 0);
+        cudaGetLastError();
+        p = nullptr;
+        e = cudaMallocAsync(&p, bytes, s);
+    }
     if (e != cudaSuccess || !p) {
         cudaGetLastError();
         fail(PAULIB_ERR_OOM, "cudaMallocAsync(" + std::to_string(bytes) + ") failed: " + cudaGetErrorString(e));
@@ -138,13 +150,7 @@ void* scratch_alloc(size_t bytes, cudaStream_t s) {
             return p;
         }
     }
-    try {
-        return dev_alloc(bytes, s);
-    } catch (const Error& e) {
-        if (e.status != PAULIB_ERR_OOM) throw;
-        scratch_cache_flush();  // give the cached blocks back and try once more
-        return dev_alloc(bytes, s);
-    }
+    return dev_alloc(bytes, s);  // on running out of memory it flushes this cache and retries
 }
 
 void scratch_free(void* p, size_t bytes, cudaStream_t s) {
