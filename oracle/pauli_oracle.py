@@ -36,6 +36,9 @@ def _load():
         lib.oracle_result_copy.argtypes = [ctypes.c_void_p, _u64p, _u64p, _f64p, _f64p, _i64p]
         lib.oracle_result_free.argtypes = [ctypes.c_void_p]
         lib.oracle_compensated_sum.restype = ctypes.c_double
+        lib.oracle_rotate.restype = ctypes.c_void_p
+        lib.oracle_rotate.argtypes = [ctypes.c_int, ctypes.c_int64, _u64p, _u64p, _f64p, _u8p, _u64p, _u64p,
+                                      ctypes.c_double, ctypes.c_double]
         _lib = lib
     return _lib
 
@@ -162,3 +165,37 @@ def compensated_sum(v):
     lib = _load()
     v = np.ascontiguousarray(v, dtype=np.float64)
     return lib.oracle_compensated_sum(ctypes.c_int64(v.size), _p(v, _f64p))
+
+
+GATES = {"h": 0, "s": 1, "cnot": 2, "cz": 3}
+
+
+def apply_clifford(n, s, gate, q1, q2=0):
+    """Conjugation U Q U^dagger of every term of ``s`` = (x, z, c[, k]) by a
+    Clifford gate ("h", "s", "cnot" with control q1 and target q2, "cz"), from
+    the gate's matrix (Sec. III-B).  Terms keep their order; returns
+    (x, z, c) with the input phase and the image's sign folded into c."""
+    lib = _load()
+    x, z, c, k, m = _prep(n, *s[:3], s[3] if len(s) > 3 else None)
+    W = _words(n)
+    ox = np.zeros((W, m), np.uint64)
+    oz = np.zeros((W, m), np.uint64)
+    oc = np.zeros(m, np.complex128)
+    lib.oracle_apply_clifford(int(n), ctypes.c_int64(m), _p(x, _u64p), _p(z, _u64p), _p(c, _f64p), _p(k, _u8p),
+                              int(GATES[gate]), int(q1), int(q2), _p(ox, _u64p), _p(oz, _u64p),
+                              _p(oc.view(np.float64), _f64p))
+    return ox, oz, oc
+
+
+def rotate(n, s, px, pz, theta, threshold=0.0):
+    """Conjugation of every term by U_P(theta) = exp(-i theta P / 2), merged
+    into canonical form, then truncated at |c| < threshold (when > 0):
+    (x, z, c, abs_sum, count)."""
+    lib = _load()
+    x, z, c, k, m = _prep(n, *s[:3], s[3] if len(s) > 3 else None)
+    W = _words(n)
+    px = np.ascontiguousarray(px, dtype=np.uint64).reshape(W)
+    pz = np.ascontiguousarray(pz, dtype=np.uint64).reshape(W)
+    h = lib.oracle_rotate(int(n), ctypes.c_int64(m), _p(x, _u64p), _p(z, _u64p), _p(c, _f64p), _p(k, _u8p),
+                          _p(px, _u64p), _p(pz, _u64p), float(theta), float(threshold))
+    return _take(ctypes.c_void_p(h), W)

@@ -169,7 +169,7 @@ Cplx load_coef(const double* c, int64_t t) { return {c[2 * t], c[2 * t + 1]}; }
 
 extern "C" {
 
-int oracle_abi_version(void) { return 1; }
+int oracle_abi_version(void) { return 2; }
 
 // Single-qubit product; letters 0=I, 1=X, 2=Y, 3=Z.
 void oracle_letter_product(int a, int b, int* out_letter, int* out_k) {
@@ -329,6 +329,187 @@ void oracle_query_product_coeffs(int n, int64_t na, const uint64_t* ax, const ui
 
 // Compensated sum of n doubles (exposed so the tests can pin the summation
 // against a correctly rounded library sum).
+// ---------------------------------------------------------------- gates
+//
+// Conjugation Q' = U Q U^dagger of every term by a Clifford gate (Sec. III-B,
+// Eq. for the conjugation; gate application of Sec. VI): the gate's 2x2 or 4x4
+// matrix is applied to the local Pauli matrix of the qubits it acts on, and
+// the image is decomposed back into Pauli letters by traces.  Gates: 0 = H,
+// 1 = S, 2 = CNOT (control q1, target q2), 3 = CZ (q1, q2).  Terms keep their
+// order; the output coefficient folds in the input phase i^k and the image's
+// sign.  Matrices act with qubit q1 as the first tensor factor.
+
+namespace {
+
+struct CM { double re, im; };
+CM cm(double r, double i) { return {r, i}; }
+CM cadd(CM a, CM b) { return {a.re + b.re, a.im + b.im}; }
+CM cmulm(CM a, CM b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+CM cconj(CM a) { return {a.re, -a.im}; }
+
+// The paper's Pauli matrices (Sec. III-A): I, X, Y = [[0,-i],[i,0]], Z.
+void pauli_matrix(int letter, CM m[2][2]) {
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) m[r][c] = cm(0, 0);
+    switch (letter) {
+        case I_: m[0][0] = cm(1, 0); m[1][1] = cm(1, 0); break;
+        case X_: m[0][1] = cm(1, 0); m[1][0] = cm(1, 0); break;
+        case Y_: m[0][1] = cm(0, -1); m[1][0] = cm(0, 1); break;
+        default: m[0][0] = cm(1, 0); m[1][1] = cm(-1, 0); break;
+    }
+}
+
+// d x d matrices, d = 2 or 4, stored row-major in a 16-entry array.
+void local_matrix(const int* letters, int nq, CM* out) {
+    CM a[2][2], b[2][2];
+    pauli_matrix(letters[0], a);
+    if (nq == 1) {
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 2; ++c) out[r * 2 + c] = a[r][c];
+        return;
+    }
+    pauli_matrix(letters[1], b);
+    for (int r1 = 0; r1 < 2; ++r1)
+        for (int c1 = 0; c1 < 2; ++c1)
+            for (int r2 = 0; r2 < 2; ++r2)
+                for (int c2 = 0; c2 < 2; ++c2) out[(r1 * 2 + r2) * 4 + (c1 * 2 + c2)] = cmulm(a[r1][c1], b[r2][c2]);
+}
+
+void gate_matrix(int gate, CM* u) {
+    const double h = 1.0 / std::sqrt(2.0);
+    for (int q = 0; q < 16; ++q) u[q] = cm(0, 0);
+    switch (gate) {
+        case 0: u[0] = cm(h, 0); u[1] = cm(h, 0); u[2] = cm(h, 0); u[3] = cm(-h, 0); break;  // H
+        case 1: u[0] = cm(1, 0); u[3] = cm(0, 1); break;                                      // S = diag(1, i)
+        case 2:  // CNOT: |c t> -> |c, t xor c>
+            u[0 * 4 + 0] = cm(1, 0); u[1 * 4 + 1] = cm(1, 0); u[3 * 4 + 2] = cm(1, 0); u[2 * 4 + 3] = cm(1, 0);
+            break;
+        default:  // CZ = diag(1, 1, 1, -1)
+            u[0] = cm(1, 0); u[5] = cm(1, 0); u[10] = cm(1, 0); u[15] = cm(-1, 0);
+            break;
+    }
+}
+
+void matmul(const CM* a, const CM* b, CM* c, int d) {
+    for (int r = 0; r < d; ++r)
+        for (int k = 0; k < d; ++k) {
+            CM s = cm(0, 0);
+            for (int q = 0; q < d; ++q) s = cadd(s, cmulm(a[r * d + q], b[q * d + k]));
+            c[r * d + k] = s;
+        }
+}
+
+// Image of the local letters under the gate: new letters and the exponent e
+// of the factor i^e (the image is i^e times a Pauli product).
+void conjugate_local(int gate, const int* letters, int nq, int* out_letters, int* e) {
+    const int d = nq == 1 ? 2 : 4;
+    CM u[16], m[16], t[16], r[16], ud[16];
+    gate_matrix(gate, u);
+    local_matrix(letters, nq, m);
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) ud[a * d + b] = cconj(u[b * d + a]);
+    matmul(u, m, t, d);
+    matmul(t, ud, r, d);
+    int found = 0;
+    for (int cand = 0; cand < (nq == 1 ? 4 : 16); ++cand) {
+        int cl[2] = {nq == 1 ? cand : cand / 4, cand % 4};
+        CM p[16];
+        local_matrix(cl, nq, p);
+        CM tr = cm(0, 0);  // Tr(p^dagger r) / d
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) tr = cadd(tr, cmulm(cconj(p[b * d + a]), r[b * d + a]));
+        tr.re /= d; tr.im /= d;
+        if (std::hypot(tr.re, tr.im) < 0.5) continue;
+        int k;
+        if (tr.re > 0.5) k = 0; else if (tr.im > 0.5) k = 1; else if (tr.re < -0.5) k = 2; else k = 3;
+        out_letters[0] = cl[0];
+        if (nq == 2) out_letters[1] = cl[1];
+        *e = k;
+        ++found;
+    }
+    if (found != 1) std::abort();
+}
+
+}  // namespace
+
+void oracle_apply_clifford(int n, int64_t nt, const uint64_t* xs, const uint64_t* zs, const double* cs,
+                           const uint8_t* kin, int gate, int q1, int q2, uint64_t* ox, uint64_t* oz,
+                           double* oc) {
+    const int W = words_for(n);
+    const int nq = gate >= 2 ? 2 : 1;
+    for (int64_t t = 0; t < nt; ++t) {
+        Str s = load_term(W, nt, xs, zs, t);
+        int letters[2] = {decode(get_bit(s.x.data(), q1), get_bit(s.z.data(), q1)),
+                          nq == 2 ? decode(get_bit(s.x.data(), q2), get_bit(s.z.data(), q2)) : 0};
+        int nl[2] = {0, 0}, e = 0;
+        conjugate_local(gate, letters, nq, nl, &e);
+        const int qs[2] = {q1, q2};
+        for (int j = 0; j < nq; ++j) {
+            int xb, zb;
+            encode(nl[j], &xb, &zb);
+            const uint64_t bit = 1ull << (qs[j] % 64);
+            s.x[qs[j] / 64] = xb ? (s.x[qs[j] / 64] | bit) : (s.x[qs[j] / 64] & ~bit);
+            s.z[qs[j] / 64] = zb ? (s.z[qs[j] / 64] | bit) : (s.z[qs[j] / 64] & ~bit);
+        }
+        for (int w = 0; w < W; ++w) { ox[(int64_t)w * nt + t] = s.x[w]; oz[(int64_t)w * nt + t] = s.z[w]; }
+        Cplx c = rot(load_coef(cs, t), (kin ? kin[t] : 0) + e);
+        oc[2 * t] = c.re; oc[2 * t + 1] = c.im;
+    }
+}
+
+// Conjugation by the Pauli rotation U_P(theta) = exp(-i theta P / 2) (Sec.
+// III-B): a term Q that commutes with P is kept; one that anti-commutes
+// becomes cos(theta) Q - i sin(theta) P Q (Eq. for the non-Clifford case).
+// Whether Q and P commute is read qubit by qubit: they anti-commute at a qubit
+// where both letters are non-identity and differ, and Q, P anti-commute when
+// that happens at an odd number of qubits (Sec. III-D).  The result is merged
+// into canonical form (Sec. III-G) and, when threshold > 0, merged terms with
+// |c| < threshold are dropped (truncation, Sec. III-B).  P is one string
+// (W words of x and of z).
+void* oracle_rotate(int n, int64_t nt, const uint64_t* xs, const uint64_t* zs, const double* cs,
+                    const uint8_t* kin, const uint64_t* px, const uint64_t* pz, double theta,
+                    double threshold) {
+    const int W = words_for(n);
+    Str P;
+    P.x.assign(px, px + W);
+    P.z.assign(pz, pz + W);
+    const double cth = std::cos(theta), sth = std::sin(theta);
+    std::map<std::vector<uint64_t>, Acc> m;
+    auto add = [&](const Str& s, Cplx c) {
+        Acc& acc = m[key_of(s)];
+        acc.re.add(c.re); acc.im.add(c.im);
+        acc.abs_sum += std::hypot(c.re, c.im);
+        acc.count += 1;
+    };
+    for (int64_t t = 0; t < nt; ++t) {
+        Str q = load_term(W, nt, xs, zs, t);
+        Cplx c = rot(load_coef(cs, t), kin ? kin[t] : 0);
+        int anti = 0;
+        for (int b = 0; b < n; ++b) {
+            int lp = decode(get_bit(P.x.data(), b), get_bit(P.z.data(), b));
+            int lq = decode(get_bit(q.x.data(), b), get_bit(q.z.data(), b));
+            if (lp != I_ && lq != I_ && lp != lq) anti ^= 1;
+        }
+        if (!anti) { add(q, c); continue; }
+        add(q, Cplx{cth * c.re, cth * c.im});
+        Str pq;
+        int k = string_product(n, P, q, &pq);           // P Q = i^k R
+        Cplx s2 = rot(Cplx{sth * c.re, sth * c.im}, 3 + k);  // -i sin(theta) c i^k
+        add(pq, s2);
+    }
+    Result* r = new Result; r->n = n; r->W = W;
+    for (const auto& kv : m) {
+        const double re = kv.second.re.value(), im = kv.second.im.value();
+        if (threshold > 0 && std::hypot(re, im) < threshold) continue;
+        r->keys.push_back(kv.first);
+        r->coef.push_back(re);
+        r->coef.push_back(im);
+        r->abs_sum.push_back(kv.second.abs_sum);
+        r->count.push_back(kv.second.count);
+    }
+    return r;
+}
+
 double oracle_compensated_sum(int64_t n, const double* v) {
     Neumaier s;
     for (int64_t t = 0; t < n; ++t) s.add(v[t]);
