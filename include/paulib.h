@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define PAULIB_ABI_VERSION 1
+#define PAULIB_ABI_VERSION 2
 #define PAULIB_MAX_QUBITS 1024
 
 typedef struct paulib_sum paulib_sum;
@@ -214,6 +214,46 @@ paulib_status paulib_multiply_noalloc(int32_t n_qubits, int64_t na, const uint64
  * range_ctas_per_sm" are applied first (the file the autotuner writes).     */
 paulib_status paulib_set_tuning(int32_t key_words, int32_t coarse_factor, int32_t oversample,
                                 int32_t count_ctas_per_sm, int32_t range_ctas_per_sm);
+
+/* ---- Gates and rotations (Sec. III-B; gate application of Sec. VI).
+ * A term is c * i^phase * P where P is a Hermitian Pauli string; a gate acts
+ * by conjugation Q -> U Q U^dagger.                                          */
+typedef enum {
+    PAULIB_GATE_H = 0,    /* Hadamard on qubit q1: X <-> Z, Y -> -Y              */
+    PAULIB_GATE_S = 1,    /* phase gate diag(1, i) on q1: X -> Y, Y -> -X        */
+    PAULIB_GATE_CNOT = 2, /* control q1, target q2: X_1 -> X_1 X_2, Z_2 -> Z_1 Z_2 */
+    PAULIB_GATE_CZ = 3    /* on q1, q2: X_1 -> X_1 Z_2, X_2 -> Z_1 X_2           */
+} paulib_gate;
+
+/* Conjugates every term of `s`, in place, by the Clifford gates of a gate
+ * list applied in order (the first gate first).  `gates` is a HOST array of
+ * n_gates triples (paulib_gate, q1, q2); q2 is ignored by one-qubit gates.
+ * Each term keeps its place; strings are relabelled and coefficients change
+ * sign where the image is -P, so the number of terms never changes (Sec.
+ * III-B, Clifford case).  A canonical sum is no longer sorted afterwards and is
+ * marked non-canonical (paulib_compress restores the order).  Every term is
+ * read and written once per call, whatever the list's length.
+ * Errors: PAULIB_ERR_INVALID_ARG for a NULL sum or list, an unknown gate, a
+ * qubit outside [0, n_qubits), or q1 == q2 in a two-qubit gate; nothing is
+ * changed then.  Asynchronous on `stream`.                                    */
+paulib_status paulib_apply_clifford(paulib_sum* s, int32_t n_gates, const int32_t* gates, void* stream);
+
+/* One step of Pauli propagation under the rotation U_P(theta) =
+ * exp(-i theta P / 2) (Sec. III-B): every term Q of `s` that commutes with P
+ * is kept; every term that anti-commutes becomes cos(theta) Q and
+ * -i sin(theta) P Q (the non-Clifford case; theta = pi and pi/2 give the
+ * Pauli and Clifford cases).  The result is returned in canonical form
+ * (duplicates merged, Sec. III-G) in a new sum *out, after dropping merged
+ * terms with |c| < threshold (truncation; threshold <= 0 keeps every term,
+ * including exact zeros).
+ *   p_x, p_z: the generator P as ceil(n/64) words each, host or device
+ *     memory (bit q%64 of word q/64 = qubit q; bits >= n_qubits must be 0).
+ *   precision: as for paulib_multiply (the merge's arithmetic).
+ * Errors: INVALID_ARG (NULL arguments), TAIL_BITS (a generator bit at a
+ * qubit >= n_qubits), UNSUPPORTED (2^32 or more terms after the split),
+ * OOM, CUDA.  Synchronises `stream` (the output size is data dependent).     */
+paulib_status paulib_rotate(const paulib_sum* s, const uint64_t* p_x, const uint64_t* p_z, double theta,
+                            double threshold, int32_t precision, void* stream, paulib_sum** out);
 
 /* Diagnostics (no counterpart in the paper): device time of the library's
  * stages measured with CUDA events recorded on the launching stream, and the

@@ -582,6 +582,55 @@ paulib_status paulib_compress(const paulib_sum* in, int32_t precision, void* str
     PAULIB_API_END
 }
 
+paulib_status paulib_apply_clifford(paulib_sum* s, int32_t n_gates, const int32_t* gates, void* stream) {
+    PAULIB_API_BEGIN
+    if (!s) fail(PAULIB_ERR_INVALID_ARG, "NULL sum");
+    if (n_gates < 0) fail(PAULIB_ERR_INVALID_ARG, "n_gates < 0");
+    if (n_gates > 0 && !gates) fail(PAULIB_ERR_INVALID_ARG, "NULL gate list");
+    for (int32_t g = 0; g < n_gates; ++g) {
+        const int32_t gate = gates[3 * g], q1 = gates[3 * g + 1], q2 = gates[3 * g + 2];
+        if (gate < PAULIB_GATE_H || gate > PAULIB_GATE_CZ)
+            fail(PAULIB_ERR_INVALID_ARG, "unknown gate " + std::to_string(gate) + " at position " + std::to_string(g));
+        const bool two = gate == PAULIB_GATE_CNOT || gate == PAULIB_GATE_CZ;
+        if (q1 < 0 || q1 >= s->n_qubits || (two && (q2 < 0 || q2 >= s->n_qubits)))
+            fail(PAULIB_ERR_INVALID_ARG, "gate " + std::to_string(g) + " acts outside the sum's qubits");
+        if (two && q1 == q2) fail(PAULIB_ERR_INVALID_ARG, "two-qubit gate " + std::to_string(g) + " with q1 == q2");
+    }
+    apply_clifford(s, n_gates, gates, (cudaStream_t)stream);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_rotate(const paulib_sum* s, const uint64_t* p_x, const uint64_t* p_z, double theta,
+                            double threshold, int32_t precision, void* stream, paulib_sum** out) {
+    if (out) *out = nullptr;
+    PAULIB_API_BEGIN
+    if (!s || !p_x || !p_z || !out) fail(PAULIB_ERR_INVALID_ARG, "NULL argument");
+    check_mode(precision);
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int W = s->W, WP = s->WP;
+    std::vector<uint64_t> px(W), pz(W);
+    if (is_device_ptr(p_x) || is_device_ptr(p_z)) {
+        check_cuda(cudaMemcpyAsync(px.data(), p_x, (size_t)W * 8, cudaMemcpyDefault, st), "generator copy");
+        check_cuda(cudaMemcpyAsync(pz.data(), p_z, (size_t)W * 8, cudaMemcpyDefault, st), "generator copy");
+        check_cuda(cudaStreamSynchronize(st), "generator sync");
+    } else {
+        std::memcpy(px.data(), p_x, (size_t)W * 8);
+        std::memcpy(pz.data(), p_z, (size_t)W * 8);
+    }
+    const int tail = s->n_qubits & 63;
+    const uint64_t tail_mask = tail ? ~((1ull << tail) - 1ull) : 0ull;
+    if ((px[W - 1] | pz[W - 1]) & tail_mask) fail(PAULIB_ERR_TAIL_BITS, "a generator bit at qubit >= n_qubits is set");
+    std::vector<uint64_t> pk(2 * (size_t)WP, 0ull);  // the device key layout: x words, then z words, zero padded
+    for (int w = 0; w < W; ++w) {
+        pk[w] = px[w];
+        pk[WP + w] = pz[w];
+    }
+    *out = rotate(s, pk.data(), theta, threshold, precision, st);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
 paulib_status paulib_multiply_batched(int32_t batch, const paulib_sum* const* a,
                                       const paulib_sum* const* b, int32_t precision, void* stream,
                                       paulib_sum** out) {

@@ -1,0 +1,312 @@
+// paulib_gates.cu -- Clifford gate application and the Pauli rotation step
+// (PauLIB Sec. III-B: conjugation Q' = U Q U^dagger; gate application of
+// Sec. VI), on the library's device sums.
+//
+// A term is c * i^phase * P(x, z) with P(x, z) = i^{|x&z|} X^x Z^z, a
+// Hermitian Pauli string.  Conjugation by a Clifford gate maps P(x, z) to
+// +-P(x', z'), so a gate rewrites a few key bits and at most flips the sign of
+// the coefficient.  The bit rules follow from the gates' action on X and Z:
+//   H:    X <-> Z                          (x, z) -> (z, x)
+//   S:    X -> XZ*i (= Y), Z -> Z           z ^= x
+//   CNOT: X_c -> X_c X_t, Z_t -> Z_c Z_t    x_t ^= x_c, z_c ^= z_t
+//   CZ:   X_c -> X_c Z_t, X_t -> Z_c X_t    z_t ^= x_c, z_c ^= x_t
+// Written in the X^x Z^z product form the image carries a factor i^u
+// (u = 2xz for H, x for S, 0 for CNOT, 2 x_c x_t for CZ, from reordering the
+// factors); renormalising to P(x', z') multiplies it by
+// i^{|x&z| - |x'&z'|} over the gate's qubits.  The total exponent is 0 or 2.
+#include "paulib_pipeline.cuh"
+
+namespace paulib {
+
+// Applies the gate list to one term held in registers; returns the exponent e
+// (mod 4) with U P(x,z) U^dagger = i^e P(x',z').
+template <int WP>
+__device__ __forceinline__ uint32_t conjugate_term(uint64_t (&k)[2 * WP], const int32_t* __restrict__ ops,
+                                                   int32_t nops) {
+    uint32_t e = 0;
+    for (int32_t g = 0; g < nops; ++g) {
+        const int32_t gate = __ldg(ops + 3 * g), q1 = __ldg(ops + 3 * g + 1), q2 = __ldg(ops + 3 * g + 2);
+        const uint32_t w1 = (uint32_t)q1 >> 6, b1 = (uint32_t)q1 & 63u;
+        const uint32_t w2 = (uint32_t)q2 >> 6, b2 = (uint32_t)q2 & 63u;
+        // read the bits of qubits q1 and q2 (masks instead of runtime indexes)
+        uint64_t x1w = 0, z1w = 0, x2w = 0, z2w = 0;
+#pragma unroll
+        for (int q = 0; q < WP; ++q) {
+            const uint64_t m1 = 0ull - (uint64_t)((uint32_t)q == w1), m2 = 0ull - (uint64_t)((uint32_t)q == w2);
+            x1w |= k[q] & m1;
+            z1w |= k[WP + q] & m1;
+            x2w |= k[q] & m2;
+            z2w |= k[WP + q] & m2;
+        }
+        const uint32_t xc = (uint32_t)(x1w >> b1) & 1u, zc = (uint32_t)(z1w >> b1) & 1u;
+        const uint32_t xt = (uint32_t)(x2w >> b2) & 1u, zt = (uint32_t)(z2w >> b2) & 1u;
+        uint32_t nxc = xc, nzc = zc, nxt = xt, nzt = zt;
+        uint32_t u = 0;
+        if (gate == PAULIB_GATE_H) {
+            nxc = zc;
+            nzc = xc;
+            u = 2u * (xc & zc);
+        } else if (gate == PAULIB_GATE_S) {
+            nzc = zc ^ xc;
+            u = xc;
+        } else if (gate == PAULIB_GATE_CNOT) {
+            nxt = xt ^ xc;
+            nzc = zc ^ zt;
+        } else {  // CZ
+            nzc = zc ^ xt;
+            nzt = zt ^ xc;
+            u = 2u * (xc & xt);
+        }
+        const bool two = gate == PAULIB_GATE_CNOT || gate == PAULIB_GATE_CZ;
+        const uint32_t before = (xc & zc) + (two ? (xt & zt) : 0u);
+        const uint32_t after = (nxc & nzc) + (two ? (nxt & nzt) : 0u);
+        e = (e + u + before - after) & 3u;
+        // write the new bits back
+#pragma unroll
+        for (int q = 0; q < WP; ++q) {
+            if ((uint32_t)q == w1) {
+                k[q] = (k[q] & ~(1ull << b1)) | ((uint64_t)nxc << b1);
+                k[WP + q] = (k[WP + q] & ~(1ull << b1)) | ((uint64_t)nzc << b1);
+            }
+        }
+        if (two) {
+#pragma unroll
+            for (int q = 0; q < WP; ++q) {
+                if ((uint32_t)q == w2) {
+                    k[q] = (k[q] & ~(1ull << b2)) | ((uint64_t)nxt << b2);
+                    k[WP + q] = (k[WP + q] & ~(1ull << b2)) | ((uint64_t)nzt << b2);
+                }
+            }
+        }
+    }
+    return e;
+}
+
+// Each term is read once, conjugated by the whole gate list in registers and
+// written once: HBM traffic per term is one record read and one written,
+// whatever the number of gates.
+template <int WP>
+__global__ void __launch_bounds__(256) k_clifford(uint64_t* keys, double2* coef, uint8_t* pbase,
+                                                  const uint8_t* __restrict__ phase, int64_t n,
+                                                  const int32_t* __restrict__ ops, int32_t nops) {
+    constexpr int NW = 2 * WP;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k[NW];
+        key_load_g<NW>(keys, (uint64_t)t, k);
+        const uint32_t e = conjugate_term<WP>(k, ops, nops);
+        key_store<NW>(keys, (uint64_t)t, k);
+        if (e) {
+            const double2 c = coef[t];
+            coef[t] = make_double2(-c.x, -c.y);  // e is 2: an exact sign flip
+        }
+        pbase[t] = (uint8_t)normal_phase<WP>(k, phase ? (uint32_t)phase[t] : 0u);
+    }
+}
+
+void apply_clifford(paulib_sum* s, int32_t nops, const int32_t* ops_host, cudaStream_t st) {
+    if (nops == 0 || s->n_terms == 0) return;
+    Scratch ops((size_t)nops * 3 * sizeof(int32_t), st);
+    check_cuda(cudaMemcpyAsync(ops.p, ops_host, (size_t)nops * 3 * sizeof(int32_t), cudaMemcpyHostToDevice, st),
+               "gate list copy");
+    const int sms = device_sm_count();
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((s->n_terms + 255) / 256, (int64_t)sms * 8));
+    StageScope ss(ST_CONVERT, st);
+    note_launch(ST_CONVERT);
+#define L(WPv)                                                                                           \
+    k_clifford<WPv><<<grid, 256, 0, st>>>(s->keys, s->coef, s->pbase, s->phase, s->n_terms, ops.as<int32_t>(), \
+                                          nops)
+    PAULIB_DISPATCH_WP(s->WP, L);
+#undef L
+    check_cuda(cudaGetLastError(), "k_clifford");
+    // the keys moved: the sum keeps its terms and their order but is no longer sorted
+    s->is_canonical = 0;
+}
+
+// ---------------------------------------------------------------- Pauli rotation
+
+// Flags the terms that anti-commute with P: the symplectic inner product
+// <x|z_P> + <z|x_P> (mod 2) is 1 (Sec. III-D).
+template <int WP>
+__global__ void __launch_bounds__(256) k_rot_flags(const uint64_t* __restrict__ keys, int64_t n,
+                                                   const uint64_t* __restrict__ pk, uint8_t* flags) {
+    constexpr int NW = 2 * WP;
+    uint64_t p[NW];
+    key_load_g<NW>(pk, 0, p);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k[NW];
+        key_load_g<NW>(keys, (uint64_t)t, k);
+        uint64_t s = 0;
+#pragma unroll
+        for (int q = 0; q < WP; ++q) s ^= (k[q] & p[WP + q]) ^ (k[WP + q] & p[q]);
+        flags[t] = (uint8_t)(__popcll(s) & 1);
+    }
+}
+
+// Term t of the input, scaled by cos(theta) when it anti-commutes, to slot t
+// of the raw output.
+template <int WP>
+__global__ void __launch_bounds__(256) k_rot_copy(const uint64_t* __restrict__ keys, const double2* __restrict__ coef,
+                                                  const uint8_t* __restrict__ phase, const uint8_t* __restrict__ flags,
+                                                  int64_t n, double cth, uint64_t* okeys, double2* ocoef,
+                                                  uint8_t* ophase, uint8_t* opb) {
+    constexpr int NW = 2 * WP;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k[NW];
+        key_load_g<NW>(keys, (uint64_t)t, k);
+        key_store<NW>(okeys, (uint64_t)t, k);
+        double2 c = coef[t];
+        if (flags[t]) c = make_double2(c.x * cth, c.y * cth);
+        ocoef[t] = c;
+        const uint32_t ph = phase ? phase[t] : 0u;
+        ophase[t] = (uint8_t)ph;
+        opb[t] = (uint8_t)normal_phase<WP>(k, ph);
+    }
+}
+
+// The partner -i sin(theta) P Q of each anti-commuting term, at slot
+// n + (its rank among them).  P Q = i^k P(x_P ^ x, z_P ^ z), k from the
+// string product (Sec. III-E) with Q's own phase folded into its exponent.
+template <int WP>
+__global__ void __launch_bounds__(kChunkThreads) k_rot_partner(uint32_t nch, const uint8_t* __restrict__ flags,
+                                                             const uint64_t* __restrict__ coff,
+                                                             const uint64_t* __restrict__ keys,
+                                                             const double2* __restrict__ coef,
+                                                             const uint8_t* __restrict__ pbase,
+                                                             const uint64_t* __restrict__ pk, uint32_t p_pb,
+                                                             int64_t n, double sth, uint64_t* okeys, double2* ocoef,
+                                                             uint8_t* ophase, uint8_t* opb) {
+    constexpr int NW = 2 * WP;
+    __shared__ uint32_t s_warp[32];
+    uint64_t p[NW];
+    key_load_g<NW>(pk, 0, p);
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        for_each_flagged(c, flags, coff, s_warp, [&](uint64_t t, uint64_t d) {
+            uint64_t q[NW], o[NW];
+            key_load_g<NW>(keys, t, q);
+            const uint32_t k = string_product<WP>(p, q, p_pb, pbase[t], o);
+            const uint64_t slot = (uint64_t)n + d;
+            key_store<NW>(okeys, slot, o);
+            const double2 cq = coef[t];
+            ocoef[slot] = make_double2(cq.y * sth, -cq.x * sth);  // c * (-i sin theta)
+            ophase[slot] = (uint8_t)k;
+            opb[slot] = (uint8_t)normal_phase<WP>(o, k);
+        });
+    }
+}
+
+template <int WP>
+__global__ void __launch_bounds__(256) k_trunc_flags(const double2* __restrict__ coef, int64_t n, double thr2,
+                                                     uint8_t* flags) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const double2 c = coef[t];
+        flags[t] = (uint8_t)(c.x * c.x + c.y * c.y >= thr2);
+    }
+}
+
+// Flag scan over n slots: flags (nch * kChunk bytes, zeroed) -> coff; returns
+// the number of flagged slots (one host synchronisation).
+static uint64_t flag_offsets(const uint8_t* flags, uint32_t nch, Scratch& coff, cudaStream_t st) {
+    Scratch cnt((size_t)nch * 4, st);
+    coff = Scratch((size_t)(nch + 1) * 8, st);
+    const int sms = device_sm_count();
+    k_flag_count<<<std::max<uint32_t>(1, std::min<uint32_t>(nch, (uint32_t)sms * 8)), kChunkThreads, 0, st>>>(
+        flags, nch, cnt.as<uint32_t>());
+    k_scan_counts<<<1, 1024, 0, st>>>(cnt.as<uint32_t>(), nch, coff.as<uint64_t>());
+    note_launch(ST_COMPACT);
+    note_launch(ST_COMPACT);
+    check_cuda(cudaGetLastError(), "flag scan");
+    uint64_t total = 0;
+    check_cuda(cudaMemcpyAsync(&total, coff.as<uint64_t>() + nch, 8, cudaMemcpyDeviceToHost, st), "count copy");
+    check_cuda(cudaStreamSynchronize(st), "count sync");
+    return total;
+}
+
+template <int WP>
+static paulib_sum* rotate_wp(const paulib_sum* s, const uint64_t* pk_host, double theta, double threshold, int mode,
+                             cudaStream_t st) {
+    constexpr int NW = 2 * WP;
+    const int64_t n = s->n_terms;
+    const int sms = device_sm_count();
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8));
+    Scratch pk((size_t)NW * 8, st);
+    check_cuda(cudaMemcpyAsync(pk.p, pk_host, (size_t)NW * 8, cudaMemcpyHostToDevice, st), "generator copy");
+    uint32_t p_pb = 0;
+    for (int q = 0; q < WP; ++q) p_pb += (uint32_t)__builtin_popcountll(pk_host[q] & pk_host[WP + q]);
+    p_pb &= 3u;
+    const uint32_t nch = (uint32_t)((n + kChunk - 1) / kChunk);
+    Scratch flags((size_t)nch * kChunk, st), coff;
+    check_cuda(cudaMemsetAsync(flags.p, 0, (size_t)nch * kChunk, st), "memset flags");
+    {
+        StageScope ss(ST_CONVERT, st);
+        note_launch(ST_CONVERT);
+        k_rot_flags<WP><<<grid, 256, 0, st>>>(s->keys, n, pk.as<uint64_t>(), flags.as<uint8_t>());
+        check_cuda(cudaGetLastError(), "k_rot_flags");
+    }
+    const uint64_t anti = flag_offsets(flags.as<uint8_t>(), nch, coff, st);
+    if ((uint64_t)n + anti >= ((uint64_t)1 << 32) - 1) fail(PAULIB_ERR_UNSUPPORTED, "rotation result needs < 2^32 terms");
+    paulib_sum* raw = sum_alloc(s->n_qubits, n + (int64_t)anti, true, st);
+    {
+        StageScope ss(ST_RAW, st);
+        note_launch(ST_RAW);
+        k_rot_copy<WP><<<grid, 256, 0, st>>>(s->keys, s->coef, s->phase, flags.as<uint8_t>(), n, std::cos(theta),
+                                             raw->keys, raw->coef, raw->phase, raw->pbase);
+        if (anti) {
+            note_launch(ST_RAW);
+            k_rot_partner<WP><<<std::max<uint32_t>(1, std::min<uint32_t>(nch, (uint32_t)sms * 8)), kChunkThreads, 0,
+                                st>>>(nch, flags.as<uint8_t>(), coff.as<uint64_t>(), s->keys, s->coef, s->pbase,
+                                      pk.as<uint64_t>(), p_pb, n, std::sin(theta), raw->keys, raw->coef, raw->phase,
+                                      raw->pbase);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            sum_free(raw, st);
+            check_cuda(e, "rotation kernels");
+        }
+    }
+    paulib_sum* canon = nullptr;
+    try {
+        canon = canon_terms(raw, mode, st);
+    } catch (...) {
+        sum_free(raw, st);
+        throw;
+    }
+    sum_free(raw, st);
+    if (!(threshold > 0) || canon->n_terms == 0) return canon;
+    // truncation: drop merged terms with |c| < threshold
+    const int64_t u = canon->n_terms;
+    const uint32_t nch2 = (uint32_t)((u + kChunk - 1) / kChunk);
+    Scratch tflags((size_t)nch2 * kChunk, st), tcoff;
+    check_cuda(cudaMemsetAsync(tflags.p, 0, (size_t)nch2 * kChunk, st), "memset flags");
+    k_trunc_flags<WP><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((u + 255) / 256, (int64_t)sms * 8)), 256, 0,
+                        st>>>(canon->coef, u, threshold * threshold, tflags.as<uint8_t>());
+    note_launch(ST_COMPACT);
+    const uint64_t keep = flag_offsets(tflags.as<uint8_t>(), nch2, tcoff, st);
+    if (keep == (uint64_t)u) return canon;
+    paulib_sum* out = sum_alloc(s->n_qubits, (int64_t)keep, false, st);
+    out->is_canonical = 1;
+    if (keep > 0) {
+        StageScope ss(ST_COMPACT, st);
+        note_launch(ST_COMPACT);
+        k_compact<WP><<<std::max<uint32_t>(1, std::min<uint32_t>(nch2, (uint32_t)sms * 8)), kChunkThreads, 0, st>>>(
+            nch2, tflags.as<uint8_t>(), tcoff.as<uint64_t>(), canon->keys, canon->coef, out->keys, out->coef,
+            out->pbase);
+    }
+    cudaError_t e = cudaGetLastError();
+    sum_free(canon, st);
+    if (e != cudaSuccess) {
+        sum_free(out, st);
+        check_cuda(e, "truncation");
+    }
+    return out;
+}
+
+paulib_sum* rotate(const paulib_sum* s, const uint64_t* pk_host, double theta, double threshold, int mode,
+                   cudaStream_t st) {
+    if (s->n_terms == 0) return empty_canonical(s->n_qubits, st);
+#define L(WPv) return rotate_wp<WPv>(s, pk_host, theta, threshold, mode, st)
+    PAULIB_DISPATCH_WP(s->WP, L);
+#undef L
+    return nullptr;
+}
+
+}  // namespace paulib

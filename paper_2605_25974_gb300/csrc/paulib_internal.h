@@ -147,6 +147,11 @@ void batch_plan_launch(paulib_batch_plan* p, cudaStream_t st);
 void batch_plan_outputs(paulib_batch_plan* p, cudaStream_t st, paulib_sum** out);
 void batch_plan_destroy(paulib_batch_plan* p);
 
+// ---- gates and rotations (paulib_gates.cu)
+void apply_clifford(paulib_sum* s, int32_t nops, const int32_t* ops_host, cudaStream_t st);
+paulib_sum* rotate(const paulib_sum* s, const uint64_t* pk_host, double theta, double threshold, int mode,
+                   cudaStream_t st);
+
 // Allocation-free canonical product using the library's static scratch
 // array (see paulib_multiply_noalloc in include/paulib.h).
 void multiply_noalloc(int32_t n_qubits, int64_t na, const uint64_t* a_x, const uint64_t* a_z,

@@ -26,7 +26,9 @@ EXPORTED = ["paulib_abi_version", "paulib_sum_create", "paulib_sum_info", "pauli
             "paulib_sum_destroy", "paulib_multiply", "paulib_compress", "paulib_multiply_batched",
             "paulib_last_error", "paulib_set_allocator", "paulib_timing_enable", "paulib_timing_read",
             "paulib_multiply_noalloc", "paulib_batch_plan_create", "paulib_batch_plan_launch",
-            "paulib_batch_plan_outputs", "paulib_batch_plan_destroy", "paulib_set_tuning"]
+            "paulib_batch_plan_outputs", "paulib_batch_plan_destroy", "paulib_set_tuning",
+            "paulib_apply_clifford", "paulib_rotate"]
+GATES = {"h": 0, "s": 1, "cnot": 2, "cz": 3}
 STAGES = ["convert", "sample", "count", "scatter", "level2", "compact", "raw", "export", "leaf"]
 
 
@@ -82,6 +84,10 @@ def load(path: Optional[str] = None):
     lib.paulib_timing_enable.restype = _i32
     lib.paulib_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
     lib.paulib_timing_read.restype = _i32
+    lib.paulib_apply_clifford.argtypes = [_vp, _i32, _vp, _vp]
+    lib.paulib_apply_clifford.restype = _i32
+    lib.paulib_rotate.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _i32, _vp, ctypes.POINTER(_vp)]
+    lib.paulib_rotate.restype = _i32
     for name in ("paulib_sum_create", "paulib_sum_info", "paulib_sum_export", "paulib_multiply",
                  "paulib_compress", "paulib_multiply_batched", "paulib_set_allocator"):
         getattr(lib, name).restype = _i32
@@ -280,3 +286,31 @@ def set_tuning(key_words=0, coarse_factor=0, oversample=0, count_ctas_per_sm=0, 
     """Pipeline tuning for keys of ``key_words`` words (0 = all); 0 keeps a value."""
     _check(load().paulib_set_tuning(int(key_words), int(coarse_factor), int(oversample), int(count_ctas_per_sm),
                                     int(range_ctas_per_sm)))
+
+
+def apply_clifford(s: "PauliSum", gates, stream=None):
+    """Conjugates every term of ``s`` in place by a list of Clifford gates
+    [(gate, q1[, q2]), ...], gate in "h", "s", "cnot", "cz" (applied in order)."""
+    ops = np.zeros((len(gates), 3), np.int32)
+    for g, op in enumerate(gates):
+        ops[g, 0] = GATES[op[0]] if isinstance(op[0], str) else int(op[0])
+        ops[g, 1] = int(op[1])
+        ops[g, 2] = int(op[2]) if len(op) > 2 else 0
+    _check(load().paulib_apply_clifford(_vp(s.handle), len(gates), _vp(ops.ctypes.data), _vp(_stream(stream))))
+    if len(gates):
+        s.is_canonical = False  # relabelled strings are no longer in key order
+
+
+def rotate(s: "PauliSum", p_x, p_z, theta: float, threshold: float = 0.0, precision="fp64",
+           stream=None) -> "PauliSum":
+    """Pauli-propagation step under exp(-i theta P / 2): a new canonical sum,
+    truncated at |c| < threshold (when threshold > 0).  P is given as
+    ceil(n/64) x- and z-words (numpy arrays or device tensors)."""
+    W = _words(s.n_qubits)
+    if isinstance(p_x, np.ndarray):
+        p_x = np.ascontiguousarray(p_x, dtype=np.uint64).reshape(W)
+        p_z = np.ascontiguousarray(p_z, dtype=np.uint64).reshape(W)
+    out = _vp()
+    _check(load().paulib_rotate(_vp(s.handle), _vp(_ptr(p_x)), _vp(_ptr(p_z)), float(theta), float(threshold),
+                                _prec(precision), _vp(_stream(stream)), ctypes.byref(out)))
+    return PauliSum(out.value)

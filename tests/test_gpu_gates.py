@@ -1,0 +1,132 @@
+"""Clifford gate application and the Pauli rotation step (Sec. III-B) on the
+GPU against the CPU oracle, through the C ABI.  Keys, their order and term
+counts bit-exact; coefficients of Clifford images exact (a sign change);
+rotation coefficients within 1e-12 * sum |contribution| (FP64 merge)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    from paper_2605_25974_gb300 import paulib
+    from paper_2605_25974_gb300.build import build
+    build()
+    torch.cuda.init()
+    return paulib
+
+
+def random_terms(rng, n, m, with_phase=False):
+    from paper_2605_25974_gb300 import workloads as wl
+    x, z = wl.weighted_random(rng, n, m, 1, n)
+    c = wl.coeffs_loguniform(rng, m)
+    k = rng.integers(0, 4, m).astype(np.uint8) if with_phase else None
+    return wl.SumArrays(n, x, z, c, k)
+
+
+def random_gates(rng, n, count):
+    gates = []
+    for _ in range(count):
+        g = ["h", "s", "cnot", "cz"][rng.integers(0, 4)]
+        q1 = int(rng.integers(0, n))
+        q2 = int(rng.integers(0, n - 1))
+        q2 = q2 + 1 if q2 >= q1 else q2
+        gates.append((g, q1, q2))
+    return gates
+
+
+@pytest.mark.parametrize("n,m,ng", [(5, 40, 1), (70, 3000, 25), (130, 5000, 60), (500, 2000, 200), (64, 700, 9)])
+def test_clifford_list_vs_oracle(lib, oracle, n, m, ng):
+    rng = np.random.default_rng(11 * n + ng)
+    s = random_terms(rng, n, m, with_phase=True)
+    gates = random_gates(rng, n, ng)
+    with lib.PauliSum.from_arrays(s) as g:
+        lib.apply_clifford(g, gates)
+        assert not g.is_canonical or ng == 0
+        x, z, c, k = g.export()
+    # oracle: gate by gate, phases folded in at the first gate
+    ox, oz, oc = s.x, s.z, s.c
+    ok = s.k
+    for gate, q1, q2 in gates:
+        ox, oz, oc = oracle.apply_clifford(n, (ox, oz, oc, ok), gate, q1, q2)
+        ok = None
+    assert np.array_equal(x, ox) and np.array_equal(z, oz)
+    # the GPU keeps the term's phase byte and moves only the sign into c
+    ik = np.array([1, 1j, -1, -1j])[k]
+    assert np.array_equal((c * ik).view(np.uint64), oc.view(np.uint64)) or np.allclose(c * ik, oc, atol=0, rtol=0)
+
+
+def test_clifford_then_compress_is_canonical(lib, oracle):
+    rng = np.random.default_rng(5)
+    n = 100
+    s = random_terms(rng, n, 4000)
+    gates = random_gates(rng, n, 30)
+    with lib.PauliSum.from_arrays(s) as g:
+        lib.apply_clifford(g, gates)
+        with lib.compress(g) as gc:
+            x, z, c, _ = gc.export()
+    ox, oz, oc = s.x, s.z, s.c
+    for gate, q1, q2 in gates:
+        ox, oz, oc = oracle.apply_clifford(n, (ox, oz, oc), gate, q1, q2)
+    cx, cz, cc, cabs, _ = oracle.compress(n, (ox, oz, oc))
+    assert np.array_equal(x, cx) and np.array_equal(z, cz)
+    assert (np.abs(c - cc) <= TOL64 * cabs).all()
+
+
+def test_clifford_errors(lib):
+    from paper_2605_25974_gb300 import workloads as wl
+    a, _ = wl.tiny()
+    with lib.PauliSum.from_arrays(a) as g:
+        for bad in ([("h", 20, 0)], [("cnot", 3, 3)], [(7, 1, 2)], [("cz", -1, 2)]):
+            with pytest.raises(lib.PaulibError) as e:
+                lib.apply_clifford(g, bad)
+            assert "INVALID_ARG" in str(e.value)
+        x0, z0, c0, _ = g.export()
+        assert np.array_equal(x0, a.x)  # nothing changed
+
+
+@pytest.mark.parametrize("n,m,theta,thr", [(6, 50, 0.37, 0.0), (100, 3000, 1.1, 0.0), (200, 5000, 0.2, 1e-4),
+                                           (500, 2000, np.pi / 2, 0.0), (70, 4000, np.pi, 0.0), (64, 3000, -0.8, 1e-3)])
+def test_rotation_vs_oracle(lib, oracle, n, m, theta, thr):
+    rng = np.random.default_rng(13 * n + m)
+    s = random_terms(rng, n, m, with_phase=True)
+    # duplicates: the generator times some terms are other terms
+    p = random_terms(rng, n, 1)
+    px, pz = p.x[:, 0], p.z[:, 0]
+    with lib.PauliSum.from_arrays(s) as g, lib.rotate(g, px, pz, theta, thr) as r:
+        assert r.is_canonical
+        x, z, c, _ = r.export()
+    ox, oz, oc, oabs, _ = oracle.rotate(n, s.as_tuple(), px, pz, theta, thr)
+    assert np.array_equal(x, ox) and np.array_equal(z, oz)
+    err = np.maximum(np.abs(c.real - oc.real), np.abs(c.imag - oc.imag))
+    assert (err <= TOL64 * np.maximum(oabs, 1e-300)).all(), float(np.max(err / np.maximum(oabs, 1e-300)))
+
+
+def test_rotation_of_jw_hamiltonian_step(lib, oracle):
+    # a propagation step on a Jordan-Wigner-shaped sum: many duplicates merge
+    from paper_2605_25974_gb300 import workloads as wl
+    h = wl.jw(n=60, m=3000, seed=77)
+    px, pz = h.x[:, 5], h.z[:, 5]  # a generator drawn from the sum itself
+    with lib.PauliSum.from_arrays(h) as g, lib.rotate(g, px, pz, 0.3, 0.0, "fp32_fp64merge") as r:
+        x, z, c, _ = r.export()
+    ox, oz, oc, oabs, _ = oracle.rotate(60, h.as_tuple(), px, pz, 0.3, 0.0)
+    assert np.array_equal(x, ox) and np.array_equal(z, oz)
+    assert (np.abs(c - oc) <= 8 * 2.0 ** -24 * 2 * oabs).all()
+
+
+def test_rotation_empty_and_tail_bits(lib):
+    from paper_2605_25974_gb300 import workloads as wl
+    a, _ = wl.tiny()
+    with lib.PauliSum.from_arrays(a) as g:
+        bad = np.zeros(1, np.uint64)
+        bad[0] = 1 << 40  # qubit 40 >= n = 20
+        with pytest.raises(lib.PaulibError) as e:
+            lib.rotate(g, bad, np.zeros(1, np.uint64), 0.5)
+        assert "TAIL_BITS" in str(e.value)
+        # identity generator: every term commutes, the result is the canonical input
+        with lib.rotate(g, np.zeros(1, np.uint64), np.zeros(1, np.uint64), 0.7) as r, lib.compress(g) as cg:
+            assert np.array_equal(r.export()[0], cg.export()[0])
