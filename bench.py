@@ -215,6 +215,71 @@ def measure_outer_product(paulib, gh, gh2, h, stream, flush, reps, hbm_peak, pea
                          "bytes_per_product": 16 * WP + 16 + 2}}
 
 
+def measure_propagation(paulib, stream, flush, reps, hbm_peak, peak_src, m=8_000_000, n=500):
+    """Pauli-propagation steps on an 8M-term, 500-qubit sum of random strings
+    of weight <= 32: one 100-gate Clifford list applied in place (Sec. III-B;
+    each term is read and written once per list) and one rotation step
+    exp(-i theta P / 2) with merge and truncation."""
+    import numpy as np
+    from paper_2605_25974_gb300 import workloads as wl
+    rng = wl.rng_for(601)
+    x, z = wl.low_weight_terms(rng, n, m, 32)
+    s = wl.SumArrays(n, x, z, wl.coeffs_loguniform(rng, m))
+    g = paulib.PauliSum.from_arrays(s)
+    WP = 1
+    while WP < s.x.shape[0]:
+        WP *= 2
+    gates = []
+    for _ in range(100):
+        kind = ["h", "s", "cnot", "cz"][int(rng.integers(0, 4))]
+        q1 = int(rng.integers(0, n))
+        q2 = int((q1 + 1 + rng.integers(0, n - 1)) % n)
+        gates.append((kind, q1, q2))
+
+    class _NoClose:
+        def close(self):
+            pass
+
+    def clifford():
+        paulib.apply_clifford(g, gates, stream=stream)
+        return _NoClose()
+
+    ms_c = timed_events(clifford, stream, flush, reps)
+    # compulsory bytes: every term's key, coefficient and phase byte read, then key,
+    # coefficient and phase byte written
+    per_term = 2 * (16 * WP + 16 + 1)
+    gbs = m * per_term / (ms_c / 1e3) / 1e9
+    res = {"terms": m, "n_qubits": n,
+           "clifford": {"gates": len(gates), "ms_per_call": ms_c, "terms_per_s": m / (ms_c / 1e3),
+                        "gate_terms_per_s": m * len(gates) / (ms_c / 1e3),
+                        "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                     "frac": gbs / hbm_peak, "peak_source": peak_src, "bytes_per_term": per_term}}}
+    # one gate per pass: the HBM-bound case (the same bytes per term)
+    one = [gates[0]]
+
+    def clifford1():
+        paulib.apply_clifford(g, one, stream=stream)
+        return _NoClose()
+
+    ms_1 = timed_events(clifford1, stream, flush, reps)
+    gbs1 = m * per_term / (ms_1 / 1e3) / 1e9
+    res["clifford_single_gate"] = {"ms_per_call": ms_1, "terms_per_s": m / (ms_1 / 1e3),
+                                   "roofline": {"bound": "hbm", "achieved": gbs1, "peak": hbm_peak, "unit": "GB/s",
+                                                "frac": gbs1 / hbm_peak, "peak_source": peak_src,
+                                                "bytes_per_term": per_term}}
+    # rotation: a weight-250 generator anti-commutes with about half the terms
+    pb = wl.SumArrays(n, *wl.low_weight_terms(wl.rng_for(602), n, 1, 250), np.ones(1, np.complex128))
+    px, pz = pb.x[:, 0], pb.z[:, 0]
+    out = paulib.rotate(g, px, pz, 0.1, 1e-9)
+    u = out.n_terms
+    out.close()
+    ms_r = timed_events(lambda: paulib.rotate(g, px, pz, 0.1, 1e-9), stream, flush, max(2, reps // 2))
+    res["rotation"] = {"theta": 0.1, "threshold": 1e-9, "ms_per_step": ms_r, "terms_in": m, "terms_out": int(u),
+                       "terms_per_s": m / (ms_r / 1e3)}
+    g.close()
+    return res
+
+
 def measure_batched(paulib, stream, flush, reps, problems=4096):
     """Batched products (4,096 independent sum x sum products shaped like
     Pauli-propagation steps) as one prepared plan replayed from a CUDA graph,
@@ -473,6 +538,9 @@ def run_ours(args):
     batched = None
     if not args.no_batched:
         batched = measure_batched(paulib, stream, flush, max(3, args.steps // 2))
+    propagation = None
+    if not args.no_propagation:
+        propagation = measure_propagation(paulib, stream, flush, max(3, args.steps // 2), hbm_peak, peak_src)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -481,7 +549,7 @@ def run_ours(args):
                        "distinct_out": U, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "512 MiB flush between timed steps"},
             "roofline": roof, "outer_product": outer, "precision": precision, "symmetric": symmetric,
-            "batched": batched,
+            "batched": batched, "propagation": propagation,
             "e2e": {"value": products / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
             "gpu_launches": int(sum(stage_launches.values())),
@@ -506,6 +574,7 @@ def main():
     ap.add_argument("--workload", default="jw_hh_n200_m30000", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-products leg")
+    ap.add_argument("--no-propagation", action="store_true", help="skip the gate and rotation leg")
     ap.add_argument("--coarse-factor", type=int, default=0,
                     help="first-level fan-out of the canonicalisation (0: library default); for profiling "
                          "small cases with the range mix of large ones")

@@ -18,28 +18,26 @@
 
 namespace paulib {
 
-// Applies the gate list to one term held in registers; returns the exponent e
-// (mod 4) with U P(x,z) U^dagger = i^e P(x',z').
+constexpr int kCliffordThreads = 256;
+
+// Applies the gate list to one term held in shared memory, word-major (word
+// w of this thread's term at sk[w * kCliffordThreads]), so that a gate reads
+// and writes just the words it touches without bank conflicts; returns the
+// exponent e (mod 4) with U P(x,z) U^dagger = i^e P(x',z').
 template <int WP>
-__device__ __forceinline__ uint32_t conjugate_term(uint64_t (&k)[2 * WP], const int32_t* __restrict__ ops,
-                                                   int32_t nops) {
+__device__ __forceinline__ uint32_t conjugate_term(uint64_t* sk, const int32_t* __restrict__ ops, int32_t nops) {
     uint32_t e = 0;
     for (int32_t g = 0; g < nops; ++g) {
         const int32_t gate = __ldg(ops + 3 * g), q1 = __ldg(ops + 3 * g + 1), q2 = __ldg(ops + 3 * g + 2);
         const uint32_t w1 = (uint32_t)q1 >> 6, b1 = (uint32_t)q1 & 63u;
         const uint32_t w2 = (uint32_t)q2 >> 6, b2 = (uint32_t)q2 & 63u;
-        // read the bits of qubits q1 and q2 (masks instead of runtime indexes)
-        uint64_t x1w = 0, z1w = 0, x2w = 0, z2w = 0;
-#pragma unroll
-        for (int q = 0; q < WP; ++q) {
-            const uint64_t m1 = 0ull - (uint64_t)((uint32_t)q == w1), m2 = 0ull - (uint64_t)((uint32_t)q == w2);
-            x1w |= k[q] & m1;
-            z1w |= k[WP + q] & m1;
-            x2w |= k[q] & m2;
-            z2w |= k[WP + q] & m2;
-        }
-        const uint32_t xc = (uint32_t)(x1w >> b1) & 1u, zc = (uint32_t)(z1w >> b1) & 1u;
-        const uint32_t xt = (uint32_t)(x2w >> b2) & 1u, zt = (uint32_t)(z2w >> b2) & 1u;
+        uint64_t* x1 = sk + (size_t)w1 * kCliffordThreads;
+        uint64_t* z1 = sk + (size_t)(WP + w1) * kCliffordThreads;
+        uint64_t* x2 = sk + (size_t)w2 * kCliffordThreads;
+        uint64_t* z2 = sk + (size_t)(WP + w2) * kCliffordThreads;
+        const bool two = gate == PAULIB_GATE_CNOT || gate == PAULIB_GATE_CZ;
+        const uint32_t xc = (uint32_t)(*x1 >> b1) & 1u, zc = (uint32_t)(*z1 >> b1) & 1u;
+        const uint32_t xt = two ? (uint32_t)(*x2 >> b2) & 1u : 0u, zt = two ? (uint32_t)(*z2 >> b2) & 1u : 0u;
         uint32_t nxc = xc, nzc = zc, nxt = xt, nzt = zt;
         uint32_t u = 0;
         if (gate == PAULIB_GATE_H) {
@@ -57,43 +55,37 @@ __device__ __forceinline__ uint32_t conjugate_term(uint64_t (&k)[2 * WP], const 
             nzt = zt ^ xc;
             u = 2u * (xc & xt);
         }
-        const bool two = gate == PAULIB_GATE_CNOT || gate == PAULIB_GATE_CZ;
-        const uint32_t before = (xc & zc) + (two ? (xt & zt) : 0u);
-        const uint32_t after = (nxc & nzc) + (two ? (nxt & nzt) : 0u);
+        const uint32_t before = (xc & zc) + (xt & zt);
+        const uint32_t after = (nxc & nzc) + (nxt & nzt);
         e = (e + u + before - after) & 3u;
-        // write the new bits back
-#pragma unroll
-        for (int q = 0; q < WP; ++q) {
-            if ((uint32_t)q == w1) {
-                k[q] = (k[q] & ~(1ull << b1)) | ((uint64_t)nxc << b1);
-                k[WP + q] = (k[WP + q] & ~(1ull << b1)) | ((uint64_t)nzc << b1);
-            }
-        }
+        *x1 ^= (uint64_t)(xc ^ nxc) << b1;
+        *z1 ^= (uint64_t)(zc ^ nzc) << b1;
         if (two) {
-#pragma unroll
-            for (int q = 0; q < WP; ++q) {
-                if ((uint32_t)q == w2) {
-                    k[q] = (k[q] & ~(1ull << b2)) | ((uint64_t)nxt << b2);
-                    k[WP + q] = (k[WP + q] & ~(1ull << b2)) | ((uint64_t)nzt << b2);
-                }
-            }
+            *x2 ^= (uint64_t)(xt ^ nxt) << b2;
+            *z2 ^= (uint64_t)(zt ^ nzt) << b2;
         }
     }
     return e;
 }
 
-// Each term is read once, conjugated by the whole gate list in registers and
-// written once: HBM traffic per term is one record read and one written,
-// whatever the number of gates.
+// Each term is read once, conjugated by the whole gate list and written
+// once: HBM traffic per term is one record read and one written, whatever
+// the number of gates.
 template <int WP>
-__global__ void __launch_bounds__(256) k_clifford(uint64_t* keys, double2* coef, uint8_t* pbase,
-                                                  const uint8_t* __restrict__ phase, int64_t n,
-                                                  const int32_t* __restrict__ ops, int32_t nops) {
+__global__ void __launch_bounds__(kCliffordThreads) k_clifford(uint64_t* keys, double2* coef, uint8_t* pbase,
+                                                               const uint8_t* __restrict__ phase, int64_t n,
+                                                               const int32_t* __restrict__ ops, int32_t nops) {
     constexpr int NW = 2 * WP;
+    extern __shared__ uint64_t s_keys[];  // [NW][kCliffordThreads]
+    uint64_t* sk = s_keys + threadIdx.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         uint64_t k[NW];
         key_load_g<NW>(keys, (uint64_t)t, k);
-        const uint32_t e = conjugate_term<WP>(k, ops, nops);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) sk[(size_t)w * kCliffordThreads] = k[w];
+        const uint32_t e = conjugate_term<WP>(sk, ops, nops);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) k[w] = sk[(size_t)w * kCliffordThreads];
         key_store<NW>(keys, (uint64_t)t, k);
         if (e) {
             const double2 c = coef[t];
@@ -109,12 +101,18 @@ void apply_clifford(paulib_sum* s, int32_t nops, const int32_t* ops_host, cudaSt
     check_cuda(cudaMemcpyAsync(ops.p, ops_host, (size_t)nops * 3 * sizeof(int32_t), cudaMemcpyHostToDevice, st),
                "gate list copy");
     const int sms = device_sm_count();
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((s->n_terms + 255) / 256, (int64_t)sms * 8));
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((s->n_terms + kCliffordThreads - 1) / kCliffordThreads, (int64_t)sms * 8));
+    const size_t sm = (size_t)2 * s->WP * kCliffordThreads * 8;
     StageScope ss(ST_CONVERT, st);
     note_launch(ST_CONVERT);
-#define L(WPv)                                                                                           \
-    k_clifford<WPv><<<grid, 256, 0, st>>>(s->keys, s->coef, s->pbase, s->phase, s->n_terms, ops.as<int32_t>(), \
-                                          nops)
+#define L(WPv)                                                                                               \
+    {                                                                                                        \
+        auto kern = k_clifford<WPv>;                                                                         \
+        smem_attr(kern, sm);                                                                                 \
+        kern<<<grid, kCliffordThreads, sm, st>>>(s->keys, s->coef, s->pbase, s->phase, s->n_terms,         \
+                                                 ops.as<int32_t>(), nops);                                   \
+    }
     PAULIB_DISPATCH_WP(s->WP, L);
 #undef L
     check_cuda(cudaGetLastError(), "k_clifford");
