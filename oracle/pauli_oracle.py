@@ -199,3 +199,20 @@ def rotate(n, s, px, pz, theta, threshold=0.0):
     h = lib.oracle_rotate(int(n), ctypes.c_int64(m), _p(x, _u64p), _p(z, _u64p), _p(c, _f64p), _p(k, _u8p),
                           _p(px, _u64p), _p(pz, _u64p), float(theta), float(threshold))
     return _take(ctypes.c_void_p(h), W)
+
+
+def multiply_pairwise(n, a, b):
+    """Element-wise products a_t * b_t of equally long term lists: (x, z, c, k)."""
+    lib = _load()
+    ax, az, ac, ak, m = _prep(n, *a[:3], a[3] if len(a) > 3 else None)
+    bx, bz, bc, bk, mb = _prep(n, *b[:3], b[3] if len(b) > 3 else None)
+    assert m == mb
+    W = _words(n)
+    ox = np.zeros((W, m), np.uint64)
+    oz = np.zeros((W, m), np.uint64)
+    oc = np.zeros(m, np.complex128)
+    ok = np.zeros(m, np.uint8)
+    lib.oracle_multiply_pairwise(int(n), ctypes.c_int64(m), _p(ax, _u64p), _p(az, _u64p), _p(ac, _f64p), _p(ak, _u8p),
+                                 _p(bx, _u64p), _p(bz, _u64p), _p(bc, _f64p), _p(bk, _u8p), _p(ox, _u64p),
+                                 _p(oz, _u64p), _p(oc.view(np.float64), _f64p), _p(ok, _u8p))
+    return ox, oz, oc, ok

@@ -510,6 +510,24 @@ void* oracle_rotate(int n, int64_t nt, const uint64_t* xs, const uint64_t* zs, c
     return r;
 }
 
+// Element-wise products a_t * b_t of two equally long lists of terms (the
+// paper's single Pauli multiplication, Sec. III-A/III-E, applied pair by
+// pair): output t is the product string with phase exponent k_t (including
+// both inputs' phases) and coefficient c_a c_b.
+void oracle_multiply_pairwise(int n, int64_t nt, const uint64_t* ax, const uint64_t* az, const double* ac,
+                              const uint8_t* ka, const uint64_t* bx, const uint64_t* bz, const double* bc,
+                              const uint8_t* kb, uint64_t* ox, uint64_t* oz, double* oc, uint8_t* ok) {
+    const int W = words_for(n);
+    for (int64_t t = 0; t < nt; ++t) {
+        Str a = load_term(W, nt, ax, az, t), b = load_term(W, nt, bx, bz, t), o;
+        const int k = string_product(n, a, b, &o);
+        for (int w = 0; w < W; ++w) { ox[(int64_t)w * nt + t] = o.x[w]; oz[(int64_t)w * nt + t] = o.z[w]; }
+        const Cplx c = cmul(load_coef(ac, t), load_coef(bc, t));
+        oc[2 * t] = c.re; oc[2 * t + 1] = c.im;
+        ok[t] = (uint8_t)((k + (ka ? ka[t] : 0) + (kb ? kb[t] : 0)) & 3);
+    }
+}
+
 double oracle_compensated_sum(int64_t n, const double* v) {
     Neumaier s;
     for (int64_t t = 0; t < n; ++t) s.add(v[t]);

@@ -147,3 +147,24 @@ def test_rotation_truncation_filters_merged_terms(oracle):
     assert keep.any() and not keep.all()
     assert np.array_equal(cut[0], full[0][:, keep]) and np.array_equal(cut[1], full[1][:, keep])
     assert np.array_equal(cut[2], full[2][keep])
+
+
+def test_pairwise_products_vs_kron(oracle):
+    # element-wise products against Kronecker matrices, phases of both inputs included
+    rng = np.random.default_rng(21)
+    n, m = 3, 60
+    sa = ["".join(rng.choice(list(LETTERS), n)) for _ in range(m)]
+    sb = ["".join(rng.choice(list(LETTERS), n)) for _ in range(m)]
+    _, ax, az = parse_strings(sa)
+    _, bx, bz = parse_strings(sb)
+    ac = rng.standard_normal(m) + 1j * rng.standard_normal(m)
+    bc = rng.standard_normal(m) + 1j * rng.standard_normal(m)
+    ka = rng.integers(0, 4, m).astype(np.uint8)
+    kb = rng.integers(0, 4, m).astype(np.uint8)
+    ox, oz, oc, ok = oracle.multiply_pairwise(n, (ax, az, ac, ka), (bx, bz, bc, kb))
+    out = format_strings(n, ox, oz)
+    ik = np.array([1, 1j, -1, -1j])
+    for t in range(m):
+        lhs = ac[t] * ik[ka[t]] * string_matrix(sa[t]) @ (bc[t] * ik[kb[t]] * string_matrix(sb[t]))
+        rhs = oc[t] * ik[ok[t]] * string_matrix(out[t])
+        assert np.allclose(lhs, rhs, atol=1e-12, rtol=0)
