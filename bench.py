@@ -276,6 +276,17 @@ def measure_propagation(paulib, stream, flush, reps, hbm_peak, peak_src, m=8_000
     ms_r = timed_events(lambda: paulib.rotate(g, px, pz, 0.1, 1e-9), stream, flush, max(2, reps // 2))
     res["rotation"] = {"theta": 0.1, "threshold": 1e-9, "ms_per_step": ms_r, "terms_in": m, "terms_out": int(u),
                        "terms_per_s": m / (ms_r / 1e3)}
+    # element-wise products of two 8M-term lists (the paper's single multiplication, in bulk)
+    xb, zb = wl.low_weight_terms(wl.rng_for(603), n, m, 32)
+    gb = paulib.PauliSum.from_arrays(wl.SumArrays(n, xb, zb, wl.coeffs_loguniform(wl.rng_for(604), m)))
+    ms_p = timed_events(lambda: paulib.multiply_pairwise(g, gb), stream, flush, reps)
+    per_pair = 2 * (16 * WP + 16 + 1) + (16 * WP + 16 + 2)  # both inputs read, one raw product written
+    gbp = m * per_pair / (ms_p / 1e3) / 1e9
+    res["pairwise"] = {"pairs": m, "ms_per_call": ms_p, "ns_per_product": ms_p * 1e6 / m,
+                       "products_per_s": m / (ms_p / 1e3),
+                       "roofline": {"bound": "hbm", "achieved": gbp, "peak": hbm_peak, "unit": "GB/s",
+                                    "frac": gbp / hbm_peak, "peak_source": peak_src, "bytes_per_product": per_pair}}
+    gb.close()
     g.close()
     return res
 

@@ -215,6 +215,16 @@ paulib_status paulib_multiply_noalloc(int32_t n_qubits, int64_t na, const uint64
 paulib_status paulib_set_tuning(int32_t key_words, int32_t coarse_factor, int32_t oversample,
                                 int32_t count_ctas_per_sm, int32_t range_ctas_per_sm);
 
+/* Element-wise products: output term t = a_t * b_t, the paper's single
+ * Pauli-string multiplication (Sec. III-A, III-E) applied to |a| pairs at
+ * once.  Requires |a| == |b| and equal qubit counts.  The output is a new raw
+ * sum (*out, owned by the caller): term t holds the product string, the
+ * coefficient c_a c_b and the phase exponent k (both inputs' phases
+ * included), exactly as a raw outer-product term.
+ * Errors: INVALID_ARG (NULL, different lengths), QUBIT_MISMATCH, OOM, CUDA.
+ * Asynchronous on `stream`.                                                  */
+paulib_status paulib_multiply_pairwise(const paulib_sum* a, const paulib_sum* b, void* stream, paulib_sum** out);
+
 /* ---- Gates and rotations (Sec. III-B; gate application of Sec. VI).
  * A term is c * i^phase * P where P is a Hermitian Pauli string; a gate acts
  * by conjugation Q -> U Q U^dagger.                                          */

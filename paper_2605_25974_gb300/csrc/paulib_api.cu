@@ -582,6 +582,17 @@ paulib_status paulib_compress(const paulib_sum* in, int32_t precision, void* str
     PAULIB_API_END
 }
 
+paulib_status paulib_multiply_pairwise(const paulib_sum* a, const paulib_sum* b, void* stream, paulib_sum** out) {
+    if (out) *out = nullptr;
+    PAULIB_API_BEGIN
+    if (!a || !b || !out) fail(PAULIB_ERR_INVALID_ARG, "NULL argument");
+    if (a->n_qubits != b->n_qubits) fail(PAULIB_ERR_QUBIT_MISMATCH, "operands have different qubit counts");
+    if (a->n_terms != b->n_terms) fail(PAULIB_ERR_INVALID_ARG, "pairwise product needs |a| == |b|");
+    *out = multiply_pairwise(a, b, (cudaStream_t)stream);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
 paulib_status paulib_apply_clifford(paulib_sum* s, int32_t n_gates, const int32_t* gates, void* stream) {
     PAULIB_API_BEGIN
     if (!s) fail(PAULIB_ERR_INVALID_ARG, "NULL sum");

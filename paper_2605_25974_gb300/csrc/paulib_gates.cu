@@ -120,6 +120,49 @@ void apply_clifford(paulib_sum* s, int32_t nops, const int32_t* ops_host, cudaSt
     s->is_canonical = 0;
 }
 
+// ---------------------------------------------------------------- pair products
+
+// Output t = a_t * b_t (the single Pauli multiplication of Sec. III-A/III-E,
+// applied pair by pair): product key, phase exponent k (both inputs' phases
+// included) and coefficient c_a c_b, in the raw form.
+template <int WP>
+__global__ void __launch_bounds__(256) k_pairwise(const uint64_t* __restrict__ ak, const double2* __restrict__ ac,
+                                                  const uint8_t* __restrict__ ap, const uint64_t* __restrict__ bk,
+                                                  const double2* __restrict__ bc, const uint8_t* __restrict__ bp,
+                                                  int64_t n, uint64_t* ok, double2* oc, uint8_t* oph, uint8_t* opb) {
+    constexpr int NW = 2 * WP;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t a[NW], b[NW], o[NW];
+        key_load_g<NW>(ak, (uint64_t)t, a);
+        key_load_g<NW>(bk, (uint64_t)t, b);
+        const uint32_t k = string_product<WP>(a, b, ap[t], bp[t], o);
+        key_store<NW>(ok, (uint64_t)t, o);
+        oc[t] = cmul(ac[t], bc[t]);
+        oph[t] = (uint8_t)k;
+        opb[t] = (uint8_t)normal_phase<WP>(o, k);
+    }
+}
+
+paulib_sum* multiply_pairwise(const paulib_sum* a, const paulib_sum* b, cudaStream_t st) {
+    paulib_sum* out = sum_alloc(a->n_qubits, a->n_terms, true, st);
+    if (a->n_terms == 0) return out;
+    const int sms = device_sm_count();
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((a->n_terms + 255) / 256, (int64_t)sms * 8));
+    StageScope ss(ST_RAW, st);
+    note_launch(ST_RAW);
+#define L(WPv)                                                                                                \
+    k_pairwise<WPv><<<grid, 256, 0, st>>>(a->keys, a->coef, a->pbase, b->keys, b->coef, b->pbase, a->n_terms, \
+                                          out->keys, out->coef, out->phase, out->pbase)
+    PAULIB_DISPATCH_WP(a->WP, L);
+#undef L
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        sum_free(out, st);
+        check_cuda(e, "k_pairwise");
+    }
+    return out;
+}
+
 // ---------------------------------------------------------------- Pauli rotation
 
 // Flags the terms that anti-commute with P: the symplectic inner product

@@ -148,6 +148,7 @@ void batch_plan_outputs(paulib_batch_plan* p, cudaStream_t st, paulib_sum** out)
 void batch_plan_destroy(paulib_batch_plan* p);
 
 // ---- gates and rotations (paulib_gates.cu)
+paulib_sum* multiply_pairwise(const paulib_sum* a, const paulib_sum* b, cudaStream_t st);
 void apply_clifford(paulib_sum* s, int32_t nops, const int32_t* ops_host, cudaStream_t st);
 paulib_sum* rotate(const paulib_sum* s, const uint64_t* pk_host, double theta, double threshold, int mode,
                    cudaStream_t st);

@@ -27,7 +27,7 @@ EXPORTED = ["paulib_abi_version", "paulib_sum_create", "paulib_sum_info", "pauli
             "paulib_last_error", "paulib_set_allocator", "paulib_timing_enable", "paulib_timing_read",
             "paulib_multiply_noalloc", "paulib_batch_plan_create", "paulib_batch_plan_launch",
             "paulib_batch_plan_outputs", "paulib_batch_plan_destroy", "paulib_set_tuning",
-            "paulib_apply_clifford", "paulib_rotate"]
+            "paulib_apply_clifford", "paulib_rotate", "paulib_multiply_pairwise"]
 GATES = {"h": 0, "s": 1, "cnot": 2, "cz": 3}
 STAGES = ["convert", "sample", "count", "scatter", "level2", "compact", "raw", "export", "leaf"]
 
@@ -88,6 +88,8 @@ def load(path: Optional[str] = None):
     lib.paulib_apply_clifford.restype = _i32
     lib.paulib_rotate.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _i32, _vp, ctypes.POINTER(_vp)]
     lib.paulib_rotate.restype = _i32
+    lib.paulib_multiply_pairwise.argtypes = [_vp, _vp, _vp, ctypes.POINTER(_vp)]
+    lib.paulib_multiply_pairwise.restype = _i32
     for name in ("paulib_sum_create", "paulib_sum_info", "paulib_sum_export", "paulib_multiply",
                  "paulib_compress", "paulib_multiply_batched", "paulib_set_allocator"):
         getattr(lib, name).restype = _i32
@@ -313,4 +315,11 @@ def rotate(s: "PauliSum", p_x, p_z, theta: float, threshold: float = 0.0, precis
     out = _vp()
     _check(load().paulib_rotate(_vp(s.handle), _vp(_ptr(p_x)), _vp(_ptr(p_z)), float(theta), float(threshold),
                                 _prec(precision), _vp(_stream(stream)), ctypes.byref(out)))
+    return PauliSum(out.value)
+
+
+def multiply_pairwise(a: "PauliSum", b: "PauliSum", stream=None) -> "PauliSum":
+    """Element-wise products a_t * b_t as a new raw sum (phases kept)."""
+    out = _vp()
+    _check(load().paulib_multiply_pairwise(_vp(a.handle), _vp(b.handle), _vp(_stream(stream)), ctypes.byref(out)))
     return PauliSum(out.value)

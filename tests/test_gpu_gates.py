@@ -130,3 +130,27 @@ def test_rotation_empty_and_tail_bits(lib):
         # identity generator: every term commutes, the result is the canonical input
         with lib.rotate(g, np.zeros(1, np.uint64), np.zeros(1, np.uint64), 0.7) as r, lib.compress(g) as cg:
             assert np.array_equal(r.export()[0], cg.export()[0])
+
+
+@pytest.mark.parametrize("n,m", [(20, 1), (64, 1000), (200, 30000), (500, 100000)])
+def test_pairwise_products_bit_exact(lib, oracle, n, m):
+    rng = np.random.default_rng(n + m)
+    a = random_terms(rng, n, m, with_phase=True)
+    b = random_terms(rng, n, m, with_phase=True)
+    with lib.PauliSum.from_arrays(a) as ga, lib.PauliSum.from_arrays(b) as gb, lib.multiply_pairwise(ga, gb) as o:
+        assert o.n_terms == m and not o.is_canonical
+        x, z, c, k = o.export()
+    ox, oz, oc, ok = oracle.multiply_pairwise(n, a.as_tuple(), b.as_tuple())
+    assert np.array_equal(x, ox) and np.array_equal(z, oz) and np.array_equal(k, ok)
+    # c_a * c_b: the GPU contracts one multiply-add, the oracle does not
+    bound = 4 * 2.0 ** -53 * np.abs(a.c) * np.abs(b.c)
+    assert np.all(np.abs(c.real - oc.real) <= bound) and np.all(np.abs(c.imag - oc.imag) <= bound)
+
+
+def test_pairwise_errors(lib):
+    from paper_2605_25974_gb300 import workloads as wl
+    a, b = wl.tiny()
+    with lib.PauliSum.from_arrays(a) as ga, lib.PauliSum.from_arrays(b.subset(slice(0, 10))) as gb:
+        with pytest.raises(lib.PaulibError) as e:
+            lib.multiply_pairwise(ga, gb)
+        assert "INVALID_ARG" in str(e.value)
