@@ -2,7 +2,7 @@
 """Benchmark: merged Pauli products per second for H*H on one GB300.
 
 A step is one canonical product C = H*H (outer product of every term pair,
-then sort by symplectic key and merge duplicates, PauLIB Sec. III-G / IV-C)
+then sort by symplectic key and merge duplicates, PauLIB Sec. III-H / IV-C)
 of a seeded, synthetic Jordan-Wigner-shaped Hamiltonian, with the inputs
 already resident in HBM.  Between timed steps a 512 MiB buffer is written to
 flush L2 (the inputs are smaller than L2).  The device time of each step is

@@ -9,7 +9,7 @@
  *   - A string is stored in the binary symplectic form (x|z) (Sec. III-C,
  *     Table I: I=(0,0), Z=(0,1), X=(1,0), Y=(1,1)), packed into W = ceil(n/64)
  *     64-bit X-words and W Z-words.  Qubit q is bit q%64 of word q/64 (the
- *     paper fixes the word index, Sec. III-F; the bit order is this library's).
+ *     paper fixes the word index, Sec. III-G; the bit order is this library's).
  *     Bits at qubit >= n of the last word must be zero.
  *   - The product of two strings XORs their words; its phase i^k follows from
  *     popcounts of the words (Sec. III-E).  Concretely, with
@@ -19,7 +19,7 @@
  *     every right term, |A|*|B| products (Sec. IV-B, IV-C, V-C).
  *   - The canonical form sorts terms by a lexicographic key of the packed
  *     words and merges equal strings by adding their coefficients
- *     (Sec. III-G).  Key = (x_0..x_{W-1}, z_0..z_{W-1}) compared as unsigned
+ *     (Sec. III-H).  Key = (x_0..x_{W-1}, z_0..z_{W-1}) compared as unsigned
  *     64-bit words, word 0 most significant.  Strings whose merged coefficient
  *     is exactly zero are kept.
  *
@@ -109,7 +109,7 @@ void paulib_sum_destroy(paulib_sum* s);
  *       j*|A| + i (one block of |A| per right term, Sec. IV-C); term phase =
  *       k_a + k_b + k_pair (mod 4); coefficient c_a*c_b (not rotated).
  *       `precision` must be PAULIB_FP64.
- *   out_kind PAULIB_OUT_CANONICAL: the canonical form (Sec. III-G) of the
+ *   out_kind PAULIB_OUT_CANONICAL: the canonical form (Sec. III-H) of the
  *       product: distinct strings in ascending key order, coefficient =
  *       sum over contributing pairs of i^k c_a c_b.  Synchronises `stream`
  *       once to learn the number of distinct strings.
@@ -118,7 +118,7 @@ void paulib_sum_destroy(paulib_sum* s);
 paulib_status paulib_multiply(const paulib_sum* a, const paulib_sum* b, int32_t precision,
                               int32_t out_kind, void* stream, paulib_sum** out);
 
-/* Canonical form of one sum (Sec. III-G, sort_and_combine): a term with
+/* Canonical form of one sum (Sec. III-H, sort_and_combine): a term with
  * phase k contributes i^k * c.  Synchronises `stream` once.                 */
 paulib_status paulib_compress(const paulib_sum* in, int32_t precision, void* stream,
                               paulib_sum** out);
@@ -225,7 +225,7 @@ paulib_status paulib_set_tuning(int32_t key_words, int32_t coarse_factor, int32_
  * Asynchronous on `stream`.                                                  */
 paulib_status paulib_multiply_pairwise(const paulib_sum* a, const paulib_sum* b, void* stream, paulib_sum** out);
 
-/* ---- Gates and rotations (Sec. III-B; gate application of Sec. VI).
+/* ---- Gates and rotations (Sec. III-B; gate application of Sec. V-B).
  * A term is c * i^phase * P where P is a Hermitian Pauli string; a gate acts
  * by conjugation Q -> U Q U^dagger.                                          */
 typedef enum {
@@ -253,7 +253,7 @@ paulib_status paulib_apply_clifford(paulib_sum* s, int32_t n_gates, const int32_
  * is kept; every term that anti-commutes becomes cos(theta) Q and
  * -i sin(theta) P Q (the non-Clifford case; theta = pi and pi/2 give the
  * Pauli and Clifford cases).  The result is returned in canonical form
- * (duplicates merged, Sec. III-G) in a new sum *out, after dropping merged
+ * (duplicates merged, Sec. III-H) in a new sum *out, after dropping merged
  * terms with |c| < threshold (truncation; threshold <= 0 keeps every term,
  * including exact zeros).
  *   p_x, p_z: the generator P as ceil(n/64) words each, host or device

@@ -4,7 +4,7 @@ Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
 leg may import this module.  Every function here forwards to
 ``paulib_oracle.cpp``, the plain qubit-by-qubit definition of the Pauli-sum
 product (PauLIB Sec. III-A), its outer product (Sec. IV-C) and its canonical
-sort-and-combine form (Sec. III-G).
+sort-and-combine form (Sec. III-H).
 
 Sums are passed as numpy arrays in the paper's struct-of-arrays layout
 (Sec. IV-A): ``x``/``z`` of shape (W, M) uint64 with W = ceil(n/64),

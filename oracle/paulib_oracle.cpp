@@ -15,14 +15,14 @@
 //     example (XIZ)(ZIX) = YIY).
 //   * Qubit letters are decoded from the binary symplectic (x|z) bits of
 //     Table I: I=(0,0), Z=(0,1), X=(1,0), Y=(1,1).  Qubit q lives in word q/64
-//     (Sec. III-F), bit q%64 (least significant bit = lowest qubit; the paper
+//     (Sec. III-G), bit q%64 (least significant bit = lowest qubit; the paper
 //     fixes only the word index, this bit order is our reading).
 //   * A Pauli sum is sum_j c_j P_j with complex c_j (Eq. 2).
 //   * The product of two sums is the outer product: every left term times
 //     every right term (Sec. IV-B/IV-C).  Raw order: the block of right term j
 //     holds the products of all left terms i, i.e. raw index j*|A| + i.
 //   * Canonical form = sort by a lexicographic key of the packed words and
-//     merge adjacent duplicates by adding coefficients (Sec. III-G).  The key
+//     merge adjacent duplicates by adding coefficients (Sec. III-H).  The key
 //     is (x_0..x_{W-1}, z_0..z_{W-1}) compared as unsigned 64-bit words, word
 //     0 most significant (our reading: the paper names a lexicographic key over
 //     the packed words without fixing the word order).  Terms whose merged
@@ -332,7 +332,7 @@ void oracle_query_product_coeffs(int n, int64_t na, const uint64_t* ax, const ui
 // ---------------------------------------------------------------- gates
 //
 // Conjugation Q' = U Q U^dagger of every term by a Clifford gate (Sec. III-B,
-// Eq. for the conjugation; gate application of Sec. VI): the gate's 2x2 or 4x4
+// Eq. for the conjugation; gate application of Sec. V-B): the gate's 2x2 or 4x4
 // matrix is applied to the local Pauli matrix of the qubits it acts on, and
 // the image is decomposed back into Pauli letters by traces.  Gates: 0 = H,
 // 1 = S, 2 = CNOT (control q1, target q2), 3 = CZ (q1, q2).  Terms keep their
@@ -462,8 +462,8 @@ void oracle_apply_clifford(int n, int64_t nt, const uint64_t* xs, const uint64_t
 // becomes cos(theta) Q - i sin(theta) P Q (Eq. for the non-Clifford case).
 // Whether Q and P commute is read qubit by qubit: they anti-commute at a qubit
 // where both letters are non-identity and differ, and Q, P anti-commute when
-// that happens at an odd number of qubits (Sec. III-D).  The result is merged
-// into canonical form (Sec. III-G) and, when threshold > 0, merged terms with
+// that happens at an odd number of qubits (Sec. III-F).  The result is merged
+// into canonical form (Sec. III-H) and, when threshold > 0, merged terms with
 // |c| < threshold are dropped (truncation, Sec. III-B).  P is one string
 // (W words of x and of z).
 void* oracle_rotate(int n, int64_t nt, const uint64_t* xs, const uint64_t* zs, const double* cs,

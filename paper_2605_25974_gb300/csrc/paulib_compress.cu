@@ -1,5 +1,5 @@
 // paulib_compress.cu -- canonical form of one sum (paulib_compress,
-// PauLIB Sec. III-G sort_and_combine); the pipeline is in paulib_pipeline.cuh.
+// PauLIB Sec. III-H sort_and_combine); the pipeline is in paulib_pipeline.cuh.
 #include "paulib_pipeline.cuh"
 
 namespace paulib {

@@ -6,7 +6,7 @@
 //   [x_0 .. x_{WP-1}, z_0 .. z_{WP-1}]
 // WP is the padded word count (1, 2, 4, 8, 16 >= ceil(n/64)); padding words
 // are zero, which leaves the lexicographic order of the real words unchanged
-// (PauLIB Sec. III-G orders terms by a lexicographic key of the packed words).
+// (PauLIB Sec. III-H orders terms by a lexicographic key of the packed words).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>

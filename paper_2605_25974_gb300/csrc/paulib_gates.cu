@@ -166,7 +166,7 @@ paulib_sum* multiply_pairwise(const paulib_sum* a, const paulib_sum* b, cudaStre
 // ---------------------------------------------------------------- Pauli rotation
 
 // Flags the terms that anti-commute with P: the symplectic inner product
-// <x|z_P> + <z|x_P> (mod 2) is 1 (Sec. III-D).
+// <x|z_P> + <z|x_P> (mod 2) is 1 (Sec. III-F).
 template <int WP>
 __global__ void __launch_bounds__(256) k_rot_flags(const uint64_t* __restrict__ keys, int64_t n,
                                                    const uint64_t* __restrict__ pk, uint8_t* flags) {

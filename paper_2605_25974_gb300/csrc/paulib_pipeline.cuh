@@ -1,4 +1,4 @@
-// paulib_pipeline.cuh -- canonical form of a Pauli-sum product (PauLIB Sec. III-G
+// paulib_pipeline.cuh -- canonical form of a Pauli-sum product (PauLIB Sec. III-H
 // sort_and_combine, applied to the outer product of Sec. IV-C / V-C).
 //
 // The paper sorts an index array by the lexicographic key of the packed words
@@ -17,7 +17,7 @@
 //             the shared-memory leaf capacity is split again by splitters taken
 //             from a sample of its own records; a leaf is gathered into shared
 //             memory, sorted by (key, record) with a bitonic network, and its
-//             equal-key runs are summed (Sec. III-G's merge).  A range whose
+//             equal-key runs are summed (Sec. III-H's merge).  A range whose
 //             keys are all equal (one heavily repeated string) is reduced
 //             without sorting.  Each coarse range writes its merged terms
 //             densely to a staging buffer.
@@ -56,7 +56,7 @@ template <> __device__ __forceinline__ float2 one_v<float2>() { return make_floa
 //
 // When both operands are the same sum (sym != 0, e.g. H*H) only records with
 // i <= j exist.  P_a P_b and P_b P_a are the same string, and their phases
-// differ by 2*[a,b] (the symplectic inner product, Sec. III-D), so the pair
+// differ by 2*[a,b] (the symplectic inner product, Sec. III-F), so the pair
 // contributes i^k c_a c_b (1 + (-1)^[a,b]): twice one product when the
 // strings commute, exactly zero when they anti-commute.  The string is kept
 // either way, as in the ordered-pair form.

@@ -6,7 +6,7 @@ products as a prepared plan replayed from a CUDA graph), and checked
     (coefficient of a given string in A*B: PauLIB Sec. IV-C with the
     single-qubit table of Sec. III-A),
   * by properties that hold at any size: keys strictly increasing (Sec.
-    III-G), every sampled pair product present, the identity coefficient of
+    III-H), every sampled pair product present, the identity coefficient of
     H*H equal to sum_j c_j^2,
   * and, where the oracle finishes in seconds at full size (the streaming
     workload's single-string products, sampled batched problems), element by

@@ -1,6 +1,6 @@
 """Pins the CPU oracle to facts that do not come from the oracle itself:
 the paper's Pauli matrices and stated products (Sec. III-A), Kronecker
-products computed by numpy, the symplectic inner product (Sec. III-D),
+products computed by numpy, the symplectic inner product (Sec. III-F),
 closed forms and invariants of the Pauli algebra, and library sorting/summing.
 """
 import itertools
@@ -119,7 +119,7 @@ def test_multiword_product_matches_per_qubit_kron(oracle):
 # ------------------------------------------------------------------ commutation
 
 def symplectic_inner(sa, sb):
-    # Sec. III-D: sum over qubits of x1 z2 XOR z1 x2, mod 2
+    # Sec. III-F: sum over qubits of x1 z2 XOR z1 x2, mod 2
     s = 0
     for a, b in zip(sa, sb):
         x1, z1 = a in "XY", a in "YZ"
