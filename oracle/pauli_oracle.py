@@ -22,6 +22,7 @@ _u64p = ctypes.POINTER(ctypes.c_uint64)
 _f64p = ctypes.POINTER(ctypes.c_double)
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 _i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
 
 
 def _load():
@@ -37,6 +38,8 @@ def _load():
         lib.oracle_result_free.argtypes = [ctypes.c_void_p]
         lib.oracle_compensated_sum.restype = ctypes.c_double
         lib.oracle_rotate.restype = ctypes.c_void_p
+        lib.oracle_group_commuting.restype = ctypes.c_int64
+        lib.oracle_group_commuting.argtypes = [ctypes.c_int, ctypes.c_int64, _u64p, _u64p, _i32p]
         lib.oracle_rotate.argtypes = [ctypes.c_int, ctypes.c_int64, _u64p, _u64p, _f64p, _u8p, _u64p, _u64p,
                                       ctypes.c_double, ctypes.c_double]
         _lib = lib
@@ -216,3 +219,16 @@ def multiply_pairwise(n, a, b):
                                  _p(bx, _u64p), _p(bz, _u64p), _p(bc, _f64p), _p(bk, _u8p), _p(ox, _u64p),
                                  _p(oz, _u64p), _p(oc.view(np.float64), _f64p), _p(ok, _u8p))
     return ox, oz, oc, ok
+
+
+def group_commuting(n, x, z):
+    """Greedy first-fit commutation grouping of the strings (x, z) in their
+    order: (group index of each term as int32 (M,), number of groups)."""
+    lib = _load()
+    W = _words(n)
+    x = np.ascontiguousarray(x, dtype=np.uint64).reshape(W, -1)
+    z = np.ascontiguousarray(z, dtype=np.uint64).reshape(W, -1)
+    m = x.shape[1]
+    grp = np.zeros(m, np.int32)
+    ng = lib.oracle_group_commuting(int(n), ctypes.c_int64(m), _p(x, _u64p), _p(z, _u64p), _p(grp, _i32p))
+    return grp, int(ng)

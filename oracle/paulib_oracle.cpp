@@ -534,4 +534,44 @@ double oracle_compensated_sum(int64_t n, const double* v) {
     return s.value();
 }
 
+// Greedy commutation grouping (Sec. V-D; the sequential variant of Sec.
+// IV-C): the terms are visited in their order and each joins the first group
+// (groups numbered in the order they were opened) all of whose members commute
+// with it, or opens a new group when no group qualifies.  Two strings commute
+// when the qubits at which their letters anti-commute (both non-identity and
+// different) are even in number (Sec. III-A), read here letter by letter.
+// group[t] receives the group of term t; the return value is the number of
+// groups.  Coefficients and phases play no part.
+int64_t oracle_group_commuting(int n, int64_t nt, const uint64_t* xs, const uint64_t* zs, int32_t* group) {
+    const int W = words_for(n);
+    std::vector<uint8_t> let((size_t)nt * n);
+    for (int64_t t = 0; t < nt; ++t) {
+        const Str s = load_term(W, nt, xs, zs, t);
+        for (int b = 0; b < n; ++b)
+            let[(size_t)t * n + b] = (uint8_t)decode(get_bit(s.x.data(), b), get_bit(s.z.data(), b));
+    }
+    auto commute = [&](int64_t a, int64_t b) {
+        const uint8_t* la = &let[(size_t)a * n];
+        const uint8_t* lb = &let[(size_t)b * n];
+        int anti = 0;
+        for (int q = 0; q < n; ++q)
+            if (la[q] != I_ && lb[q] != I_ && la[q] != lb[q]) anti ^= 1;
+        return anti == 0;
+    };
+    std::vector<std::vector<int64_t>> groups;
+    for (int64_t t = 0; t < nt; ++t) {
+        size_t g = 0;
+        for (; g < groups.size(); ++g) {
+            bool fits = true;
+            for (int64_t s : groups[g])
+                if (!commute(s, t)) { fits = false; break; }
+            if (fits) break;
+        }
+        if (g == groups.size()) groups.emplace_back();
+        groups[g].push_back(t);
+        group[t] = (int32_t)g;
+    }
+    return (int64_t)groups.size();
+}
+
 }  // extern "C"

@@ -26,6 +26,10 @@ Sec. III-A, Eq. 2):
   (X/Y at p<q<r<s with Z runs inside (p,q) and (r,s)); |c| log-uniform on
   [1e-6,1], uniform phase.  n=100/M=20,000 (seed 301) and n=200/M=30,000
   (seed 401); H*H is the product.
+* ``grouping``: random n=500 sums for greedy commutation grouping (the
+  paper's grouping benchmark, Sec. VI-C, uses random 500-qubit sums of 200 to
+  2,000 terms): every qubit uniform over {I,X,Y,Z}, distinct strings,
+  re/im ~ N(0,1); seed 600 + M // 100 for M terms.
 * ``batch``: 4,096 independent products at n=500; left sizes
   floor(exp(U(ln 16, ln 16384))), right sizes uniform in 1..8, strings of
   weight at most 32 on random qubits (repeats allowed), coefficients as in
@@ -279,6 +283,12 @@ def jw(n: int = 100, m: int = 20_000, seed: int = 301) -> SumArrays:
     rng = rng_for(seed)
     x, z = jw_hamiltonian(rng, n, m)
     return SumArrays(n, x, z, coeffs_loguniform(rng, m))
+
+
+def grouping(m: int = 2000, n: int = 500, seed: Optional[int] = None) -> SumArrays:
+    rng = rng_for(600 + m // 100 if seed is None else seed)
+    x, z = uniform_letters(rng, n, m)
+    return SumArrays(n, x, z, coeffs_normal(rng, m))
 
 
 def low_weight_terms(rng: np.random.Generator, n: int, m: int, wmax: int, chunk: int = 1 << 20):

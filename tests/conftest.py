@@ -16,6 +16,18 @@ def pytest_configure(config):
 # ----------------------------------------------------------------- shared helpers
 
 LETTERS = "IXYZ"
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def read_golden(name):
+    """Rows of a golden fixture under tests/golden ('#' starts a comment)."""
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                rows.append(line.split())
+    return rows
 
 
 def parse_strings(strs):

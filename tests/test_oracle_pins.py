@@ -10,9 +10,8 @@ import os
 import numpy as np
 import pytest
 
-from conftest import LETTERS, keys_as_tuples, parse_strings, format_strings
+from conftest import LETTERS, keys_as_tuples, parse_strings, format_strings, read_golden
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 # The four Pauli matrices as printed in Sec. III-A.
 MATS = {
@@ -40,16 +39,6 @@ def oracle_product_of_strings(oracle, sa, sb):
     _, xb, zb = parse_strings([sb])
     xo, zo, k = oracle.string_product(n, xa[:, 0], za[:, 0], xb[:, 0], zb[:, 0])
     return format_strings(n, xo.reshape(-1, 1), zo.reshape(-1, 1))[0], k
-
-
-def read_golden(name):
-    rows = []
-    with open(os.path.join(GOLDEN, name)) as f:
-        for line in f:
-            line = line.split("#")[0].strip()
-            if line:
-                rows.append(line.split())
-    return rows
 
 
 # ------------------------------------------------------------------ matrices
