@@ -291,6 +291,38 @@ def measure_propagation(paulib, stream, flush, reps, hbm_peak, peak_src, m=8_000
     return res
 
 
+def measure_grouping(paulib, stream, reps, sizes=(200, 500, 1000, 2000, 20000), n=500):
+    """Greedy commutation grouping (Sec. V-D) of random 500-qubit sums, at the
+    paper's grouping sizes (200 to 2,000 terms, Sec. VI-C) and one larger sum:
+    the whole call (anti-commutation bits, the greedy walk, the group count
+    read back to the host, the CSR listing), timed with CUDA events around it
+    and with the host clock."""
+    import torch
+    from paper_2605_25974_gb300 import workloads as wl
+    out = {"n_qubits": n, "paper_cpu_ms": {"200": 0.05, "2000": 5.6}, "sizes": {}}
+    for m in sizes:
+        g = paulib.PauliSum.from_arrays(wl.grouping(m, n=n))
+        for _ in range(3):
+            paulib.group_commuting(g, csr=True, stream=stream)
+        ev, wall = [], []
+        ng = 0
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e0.record(stream)
+            _, ng, _, _ = paulib.group_commuting(g, csr=True, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            wall.append((time.perf_counter() - t0) * 1e3)
+            ev.append(e0.elapsed_time(e1))
+        ms = statistics.median(ev)
+        out["sizes"][str(m)] = {"groups": ng, "ms_per_call": ms, "ms_per_call_host": statistics.median(wall),
+                                "us_per_term": ms * 1e3 / m}
+        g.close()
+    return out
+
+
 def measure_batched(paulib, stream, flush, reps, problems=4096):
     """Batched products (4,096 independent sum x sum products shaped like
     Pauli-propagation steps) as one prepared plan replayed from a CUDA graph,
@@ -553,6 +585,10 @@ def run_ours(args):
     if not args.no_propagation:
         propagation = measure_propagation(paulib, stream, flush, max(3, args.steps // 2), hbm_peak, peak_src)
 
+    grouping = None
+    if not args.no_grouping:
+        grouping = measure_grouping(paulib, stream, max(5, args.steps))
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -560,7 +596,7 @@ def run_ours(args):
                        "distinct_out": U, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "512 MiB flush between timed steps"},
             "roofline": roof, "outer_product": outer, "precision": precision, "symmetric": symmetric,
-            "batched": batched, "propagation": propagation,
+            "batched": batched, "propagation": propagation, "grouping": grouping,
             "e2e": {"value": products / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
             "gpu_launches": int(sum(stage_launches.values())),
@@ -586,6 +622,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-products leg")
     ap.add_argument("--no-propagation", action="store_true", help="skip the gate and rotation leg")
+    ap.add_argument("--no-grouping", action="store_true", help="skip the commutation-grouping leg")
     ap.add_argument("--coarse-factor", type=int, default=0,
                     help="first-level fan-out of the canonicalisation (0: library default); for profiling "
                          "small cases with the range mix of large ones")

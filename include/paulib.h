@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define PAULIB_ABI_VERSION 2
+#define PAULIB_ABI_VERSION 3
 #define PAULIB_MAX_QUBITS 1024
 
 typedef struct paulib_sum paulib_sum;
@@ -265,18 +265,49 @@ paulib_status paulib_apply_clifford(paulib_sum* s, int32_t n_gates, const int32_
 paulib_status paulib_rotate(const paulib_sum* s, const uint64_t* p_x, const uint64_t* p_z, double theta,
                             double threshold, int32_t precision, void* stream, paulib_sum** out);
 
+/* Greedy commutation grouping (Sec. V-D; the sequential variant of Sec.
+ * IV-C): partitions the terms of `s` into groups of mutually commuting
+ * strings.  The terms are visited in their order; each joins the first group
+ * (groups are numbered in the order they are opened) all of whose members
+ * commute with it, or opens a new group when none qualifies.  Two strings
+ * commute when their symplectic inner product is even (Sec. III-F);
+ * coefficients and phases play no part, and repeated strings are fine.
+ *   group_of_term: DEVICE int32[n_terms]; receives the group of every term
+ *     (may be NULL for an empty sum).
+ *   group_offsets: NULL, or DEVICE int32[n_groups + 1] (n_terms + 1 always
+ *     suffices): the first member slot of each group, then n_terms.
+ *   members: NULL, or DEVICE int32[n_terms]: the terms of group 0 in
+ *     increasing order, then those of group 1, and so on (group g's are
+ *     members[group_offsets[g] .. group_offsets[g+1])).
+ *   n_groups: HOST; receives the number of groups.
+ * Scratch: about n_terms^2 / 16 bytes of device memory for the
+ * anti-commutation bits.
+ * Errors: INVALID_ARG (NULL sum, group_of_term or n_groups), UNSUPPORTED
+ * (more than 4,194,240 terms, or a partition into more than 32,704 groups),
+ * OOM, CUDA.  Synchronises `stream` (n_groups is returned on the host).      */
+paulib_status paulib_group_commuting(const paulib_sum* s, int32_t* group_of_term, int32_t* group_offsets,
+                                     int32_t* members, int64_t* n_groups, void* stream);
+
+/* Grouping tuning (no counterpart in the paper; results never depend on
+ * it): the number of available groups, 1..4 (default 4), that each term
+ * keeps when its 64-term block starts.  A term whose kept groups are all
+ * taken by earlier anti-commuting terms of its block scans its whole
+ * availability row instead.  Errors: INVALID_ARG outside 1..4.              */
+paulib_status paulib_set_group_candidates(int32_t k);
+
 /* Diagnostics (no counterpart in the paper): device time of the library's
  * stages measured with CUDA events recorded on the launching stream, and the
  * number of kernels launched per stage.  Stages:
  *   0 input conversion, 1 splitter sampling and selection, 2 coarse count,
  *   3 coarse scatter, 4 range splitting (the per-range worklist kernel),
- *   5 output compaction, 6 raw outer product, 7 export, 8 leaf sort + merge.
+ *   5 output compaction, 6 raw outer product, 7 export, 8 leaf sort + merge,
+ *   9 commutation grouping.
  * paulib_timing_enable(1) starts recording (0 stops).  paulib_timing_read
  * waits for recorded events, adds their times to ms[PAULIB_STAGES] and the
  * launch counts to launches[PAULIB_STAGES] (either may be NULL), and clears
  * the totals when `reset` is nonzero.  Launch counts are kept even when
  * event timing is off.                                                      */
-#define PAULIB_STAGES 9
+#define PAULIB_STAGES 10
 paulib_status paulib_timing_enable(int32_t on);
 paulib_status paulib_timing_read(double* ms, int64_t* launches, int32_t reset);
 

@@ -593,6 +593,23 @@ paulib_status paulib_multiply_pairwise(const paulib_sum* a, const paulib_sum* b,
     PAULIB_API_END
 }
 
+paulib_status paulib_group_commuting(const paulib_sum* s, int32_t* group_of_term, int32_t* group_offsets,
+                                     int32_t* members, int64_t* n_groups, void* stream) {
+    PAULIB_API_BEGIN
+    if (!s || !n_groups || (!group_of_term && s->n_terms > 0)) fail(PAULIB_ERR_INVALID_ARG, "NULL argument");
+    *n_groups = group_commuting(s, group_of_term, group_offsets, members, (cudaStream_t)stream);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_set_group_candidates(int32_t k) {
+    PAULIB_API_BEGIN
+    if (k < 1 || k > 4) fail(PAULIB_ERR_INVALID_ARG, "candidates per term must be in 1..4");
+    set_group_cands(k);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
 paulib_status paulib_apply_clifford(paulib_sum* s, int32_t n_gates, const int32_t* gates, void* stream) {
     PAULIB_API_BEGIN
     if (!s) fail(PAULIB_ERR_INVALID_ARG, "NULL sum");

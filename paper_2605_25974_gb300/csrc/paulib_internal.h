@@ -106,7 +106,7 @@ int device_sm_count();
 // outermost active scope, so nested pipelines count toward the outer stage.
 enum Stage : int {
     ST_CONVERT = 0, ST_SAMPLE = 1, ST_COUNT = 2, ST_SCATTER = 3, ST_LEVEL2 = 4, ST_COMPACT = 5,
-    ST_RAW = 6, ST_EXPORT = 7, ST_LEAF = 8
+    ST_RAW = 6, ST_EXPORT = 7, ST_LEAF = 8, ST_GROUP = 9
 };
 struct StageScope {
     StageScope(int stage, cudaStream_t s);
@@ -149,6 +149,9 @@ void batch_plan_destroy(paulib_batch_plan* p);
 
 // ---- gates and rotations (paulib_gates.cu)
 paulib_sum* multiply_pairwise(const paulib_sum* a, const paulib_sum* b, cudaStream_t st);
+// Greedy commutation grouping (paulib_group.cu); returns the number of groups.
+int64_t group_commuting(const paulib_sum* s, int32_t* group, int32_t* offsets, int32_t* members, cudaStream_t st);
+void set_group_cands(int k);
 void apply_clifford(paulib_sum* s, int32_t nops, const int32_t* ops_host, cudaStream_t st);
 paulib_sum* rotate(const paulib_sum* s, const uint64_t* pk_host, double theta, double threshold, int mode,
                    cudaStream_t st);

@@ -27,9 +27,10 @@ EXPORTED = ["paulib_abi_version", "paulib_sum_create", "paulib_sum_info", "pauli
             "paulib_last_error", "paulib_set_allocator", "paulib_timing_enable", "paulib_timing_read",
             "paulib_multiply_noalloc", "paulib_batch_plan_create", "paulib_batch_plan_launch",
             "paulib_batch_plan_outputs", "paulib_batch_plan_destroy", "paulib_set_tuning",
-            "paulib_apply_clifford", "paulib_rotate", "paulib_multiply_pairwise"]
+            "paulib_apply_clifford", "paulib_rotate", "paulib_multiply_pairwise",
+            "paulib_group_commuting", "paulib_set_group_candidates"]
 GATES = {"h": 0, "s": 1, "cnot": 2, "cz": 3}
-STAGES = ["convert", "sample", "count", "scatter", "level2", "compact", "raw", "export", "leaf"]
+STAGES = ["convert", "sample", "count", "scatter", "level2", "compact", "raw", "export", "leaf", "group"]
 
 
 class PaulibError(RuntimeError):
@@ -90,6 +91,10 @@ def load(path: Optional[str] = None):
     lib.paulib_rotate.restype = _i32
     lib.paulib_multiply_pairwise.argtypes = [_vp, _vp, _vp, ctypes.POINTER(_vp)]
     lib.paulib_multiply_pairwise.restype = _i32
+    lib.paulib_group_commuting.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(_i64), _vp]
+    lib.paulib_group_commuting.restype = _i32
+    lib.paulib_set_group_candidates.argtypes = [_i32]
+    lib.paulib_set_group_candidates.restype = _i32
     for name in ("paulib_sum_create", "paulib_sum_info", "paulib_sum_export", "paulib_multiply",
                  "paulib_compress", "paulib_multiply_batched", "paulib_set_allocator"):
         getattr(lib, name).restype = _i32
@@ -323,3 +328,27 @@ def multiply_pairwise(a: "PauliSum", b: "PauliSum", stream=None) -> "PauliSum":
     out = _vp()
     _check(load().paulib_multiply_pairwise(_vp(a.handle), _vp(b.handle), _vp(_stream(stream)), ctypes.byref(out)))
     return PauliSum(out.value)
+
+
+def group_commuting(s: "PauliSum", csr: bool = True, stream=None):
+    """Greedy first-fit partition of the terms into mutually commuting groups
+    (terms in order; each joins the first group it commutes with entirely).
+    Returns (group of each term, number of groups, offsets, members) as device
+    int32 tensors; offsets (G+1,) and members (M,) are None unless csr."""
+    import torch
+    m = s.n_terms
+    dev = torch.device("cuda", torch.cuda.current_device())
+    group = torch.empty(m, dtype=torch.int32, device=dev)
+    offsets = torch.empty(m + 1, dtype=torch.int32, device=dev) if csr else None
+    members = torch.empty(m, dtype=torch.int32, device=dev) if csr else None
+    ng = _i64(0)
+    _check(load().paulib_group_commuting(_vp(s.handle), _vp(_ptr(group)), _vp(_ptr(offsets)), _vp(_ptr(members)),
+                                         ctypes.byref(ng), _vp(_stream(stream))))
+    g = int(ng.value)
+    return group, g, (offsets[:g + 1] if csr else None), members
+
+
+def set_group_candidates(k: int):
+    """Groups each term keeps at the start of its 64-term block (1..4); the
+    partition never depends on it."""
+    _check(load().paulib_set_group_candidates(int(k)))

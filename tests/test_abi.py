@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_abi_version(lib):
     lib.paulib_abi_version.restype = ctypes.c_int32
-    assert lib.paulib_abi_version() == 2
+    assert lib.paulib_abi_version() == 3
 
 
 def test_binding_fails_loudly_without_library(tmp_path):

@@ -5,7 +5,6 @@ closed forms and invariants of the Pauli algebra, and library sorting/summing.
 """
 import itertools
 import math
-import os
 
 import numpy as np
 import pytest
