@@ -31,6 +31,8 @@
 //               so a row needs the bits of the G groups so far plus 64.
 //   k_group_csr the members of each group in term order (optional).
 #include <atomic>
+#include <climits>
+#include <type_traits>
 
 #include "paulib_pipeline.cuh"
 
@@ -171,56 +173,109 @@ __global__ void __launch_bounds__(kGreedyThreads, 1)
             }
             if (lane == 0) s_ncand[i] = min(found, kc + 1);
         }
-        __syncthreads();
         const bool has_next = b + 1 < nblocks;
         const uint64_t* ncol = at + anti_col_offset(b + 1);
+        __syncthreads();
         if (warp == 0) {
             // lane state for its terms t = lane (slot 0) and lane + 32 (slot 1):
-            // candidates c*, taken candidates blk (bit k), taken new groups nblk
-            // (bit k: group g0 + k), and the current choice cur (-1: scan the row)
+            // candidates c0..c3 (INT_MAX: none) with the untaken ones as bits of
+            // fr, taken new groups nblk (bit k: group g0 + k), and the current
+            // choice cur: a group id, -1 for the lowest untaken new group (one-hot
+            // in noh), -2 when the row must be scanned.  The per-term chain uses
+            // only shuffles, compares, selects and adds: find-first-set and
+            // popcount cost tens of cycles each and stay off it.
             int c0[2], c1[2], c2[2], c3[2], cur[2], fin[2];
-            uint32_t valid[2], blk[2];
+            uint32_t fr[2];
             bool more[2];
-            uint64_t nblk[2], drow[2], a[2];
+            uint64_t nblk[2], noh[2], foh[2], drow[2], a[2];
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 const int t = lane + 32 * s;
                 const bool on = t < nb;
                 const int nc = on ? s_ncand[t] : 0;
                 const int kk = min(nc, kc);
-                c0[s] = kk > 0 ? s_cand[t][0] : -1;
-                c1[s] = kk > 1 ? s_cand[t][1] : -1;
-                c2[s] = kk > 2 ? s_cand[t][2] : -1;
-                c3[s] = kk > 3 ? s_cand[t][3] : -1;
-                valid[s] = (1u << kk) - 1u;
+                c0[s] = kk > 0 ? s_cand[t][0] : INT_MAX;
+                c1[s] = kk > 1 ? s_cand[t][1] : INT_MAX;
+                c2[s] = kk > 2 ? s_cand[t][2] : INT_MAX;
+                c3[s] = kk > 3 ? s_cand[t][3] : INT_MAX;
+                fr[s] = (1u << kk) - 1u;
                 more[s] = nc > kc;
-                blk[s] = 0;
                 nblk[s] = 0ull;
-                cur[s] = kk > 0 ? c0[s] : (more[s] ? -1 : g0);
+                noh[s] = 1ull;
+                cur[s] = kk > 0 ? c0[s] : (more[s] ? -2 : -1);
                 fin[s] = 0;
+                foh[s] = 0ull;
                 drow[s] = on ? s_diag[t] : 0ull;
                 a[s] = on && has_next ? ncol[t0 + t] : 0ull;
             }
-            int ng = g0;
-            uint64_t d = s_diag[0];
-            for (int i = 0; i < nb; ++i) {
-                const int sl = i >> 5, owner = i & 31;
-                // anti-commutation of term i with this lane's terms (bits j > i of its row)
-                const bool an0 = (uint32_t)(d >> lane) & 1u;
-                const bool an1 = (uint32_t)(d >> 32 >> lane) & 1u;
-                if (i + 1 < nb) d = s_diag[i + 1];
-                int g = __shfl_sync(FULL, sl ? cur[1] : cur[0], owner);
-                if (g < 0) {
+            // term i chose (g, oh): g a group id, or -1 with oh the new group's bit.
+            // Record it; the later terms that anti-commute with term i (an*) lose
+            // it and recompute their choice.  Selects only, no branches.
+            auto apply = [&](auto both, int i, int g, uint64_t oh, bool an0, bool an1) {
+                const bool mine = lane == (i & 31);
+                fin[0] = mine && i < 32 ? g : fin[0];
+                foh[0] = mine && i < 32 ? oh : foh[0];
+                fin[1] = mine && i >= 32 ? g : fin[1];
+                foh[1] = mine && i >= 32 ? oh : foh[1];
+#pragma unroll
+                for (int s = decltype(both)::value ? 0 : 1; s < 2; ++s) {
+                    const bool an = s ? an1 : an0;
+                    const uint32_t hit = (uint32_t)(c0[s] == g) | ((uint32_t)(c1[s] == g) << 1) |
+                                         ((uint32_t)(c2[s] == g) << 2) | ((uint32_t)(c3[s] == g) << 3);
+                    fr[s] &= an ? ~hit : ~0u;
+                    nblk[s] |= an ? oh : 0ull;
+                    noh[s] = ~nblk[s] & (nblk[s] + 1ull);
+                    const uint32_t f = fr[s];
+                    const int c = (f & 1u) ? c0[s] : (f & 2u) ? c1[s] : (f & 4u) ? c2[s] : c3[s];
+                    cur[s] = f ? c : (more[s] ? -2 : -1);
+                }
+            };
+            auto anti = [&](int i, bool& an0, bool& an1) {
+                const uint64_t d = s_diag[i];
+                an0 = (uint32_t)(d >> lane) & 1u;
+                an1 = (uint32_t)(d >> 32 >> lane) & 1u;
+            };
+            int i = 0;
+            while (i < nb) {
+                // the hot loops: the owner's choice by shuffle, then the update
+                bool an0, an1;
+                anti(i, an0, an1);
+                for (; i < min(nb, 32); ++i) {
+                    const int g = __shfl_sync(FULL, cur[0], i);
+                    const uint32_t ohl = __shfl_sync(FULL, (uint32_t)noh[0], i);
+                    const uint32_t ohh = __shfl_sync(FULL, (uint32_t)(noh[0] >> 32), i);
+                    if (g == -2) break;
+                    bool n0, n1;
+                    anti(i + 1 < nb ? i + 1 : i, n0, n1);
+                    apply(std::true_type(), i, g, g < 0 ? ((uint64_t)ohh << 32 | ohl) : 0ull, an0, an1);
+                    an0 = n0;
+                    an1 = n1;
+                }
+                if (i >= 32 || i == nb) {
+                    for (; i < nb; ++i) {
+                        const int g = __shfl_sync(FULL, cur[1], i & 31);
+                        const uint32_t ohl = __shfl_sync(FULL, (uint32_t)noh[1], i & 31);
+                        const uint32_t ohh = __shfl_sync(FULL, (uint32_t)(noh[1] >> 32), i & 31);
+                        if (g == -2) break;
+                        bool n0, n1;
+                        anti(i + 1 < nb ? i + 1 : i, n0, n1);
+                        apply(std::false_type(), i, g, g < 0 ? ((uint64_t)ohh << 32 | ohl) : 0ull, an0, an1);
+                        an0 = n0;
+                        an1 = n1;
+                    }
+                }
+                if (i < nb) {
                     // every kept candidate of term i is taken: clear from its row the
                     // groups chosen by earlier anti-commuting terms, take the first left
 #pragma unroll
                     for (int s = 0; s < 2; ++s) {
                         const int j = lane + 32 * s;
-                        if (j < i && ((drow[s] >> i) & 1ull) && fin[s] < g0)
+                        if (j < i && ((drow[s] >> i) & 1ull) && fin[s] >= 0)
                             atomicAnd(reinterpret_cast<unsigned long long*>(avail + i * AVS + (fin[s] >> 6)),
                                       ~(1ull << (fin[s] & 63)));
                     }
                     __syncwarp();
+                    int g = -1;
                     for (int w0 = 0; w0 < wx && g < 0; w0 += 32) {
                         const uint64_t word = w0 + lane < wx ? avail[i * AVS + w0 + lane] : 0ull;
                         const uint32_t bal = __ballot_sync(FULL, word != 0ull);
@@ -230,47 +285,35 @@ __global__ void __launch_bounds__(kGreedyThreads, 1)
                             g = (w0 + fl) * 64 + __ffsll((long long)v) - 1;
                         }
                     }
-                    const uint64_t nbk = __shfl_sync(FULL, sl ? nblk[1] : nblk[0], owner);
-                    if (g < 0) g = g0 + __ffsll((long long)~nbk) - 1;
-                }
-                ng = max(ng, g + 1);
-                const bool mine = lane == owner;
-                fin[0] = mine && !sl ? g : fin[0];
-                fin[1] = mine && sl ? g : fin[1];
-                // terms that anti-commute with term i lose group g; recompute their choice
-                const bool isnew = g >= g0;
-                const uint64_t nbit = 1ull << ((g - g0) & 63);
-#pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    const bool an = s ? an1 : an0;
-                    const uint32_t hit = (uint32_t)(c0[s] == g) | ((uint32_t)(c1[s] == g) << 1) |
-                                         ((uint32_t)(c2[s] == g) << 2) | ((uint32_t)(c3[s] == g) << 3);
-                    blk[s] |= an ? hit : 0u;
-                    nblk[s] |= (an && isnew) ? nbit : 0ull;
-                    const uint32_t free = valid[s] & ~blk[s];
-                    const int k = __ffs(free) - 1;
-                    const int c = k <= 1 ? (k == 0 ? c0[s] : c1[s]) : (k == 2 ? c2[s] : c3[s]);
-                    const int nw = g0 + __ffsll((long long)~nblk[s]) - 1;
-                    cur[s] = free ? c : (more[s] ? -1 : nw);
+                    const uint64_t oh = __shfl_sync(FULL, i >= 32 ? noh[1] : noh[0], i & 31);
+                    anti(i, an0, an1);
+                    if (i < 32) apply(std::true_type(), i, g, g < 0 ? oh : 0ull, an0, an1);
+                    else apply(std::false_type(), i, g, g < 0 ? oh : 0ull, an0, an1);
+                    ++i;
                 }
             }
-            // the block's results, and their words of column b+1 into the next masks
+            // the block's results (new groups numbered from their bits), and their
+            // words of column b+1 into the next masks
+            int top = g0 - 1;
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 const int t = lane + 32 * s;
                 if (t < nb) {
-                    group[t0 + t] = fin[s];
-                    if (a[s]) atomicOr(reinterpret_cast<unsigned long long*>(nnxt + fin[s]), (unsigned long long)a[s]);
+                    const int gf = fin[s] >= 0 ? fin[s] : g0 + __ffsll((long long)foh[s]) - 1;
+                    top = max(top, gf);
+                    group[t0 + t] = gf;
+                    if (a[s]) atomicOr(reinterpret_cast<unsigned long long*>(nnxt + gf), (unsigned long long)a[s]);
                 }
             }
-            if (lane == 0) s_groups = ng;
+            top = __reduce_max_sync(FULL, top);
+            if (lane == 0) s_groups = top + 1;
         } else {
-            // the masks just transposed are block b+2's accumulator: clear them
+            // meanwhile: the masks just transposed become block b+2's accumulator
+            // (cleared), and every earlier term's column-(b+1) word goes into its
+            // group's mask for block b+1
             const int ht = tid - 32, hn = kGreedyThreads - 32;
             for (int g = ht; g < g0; g += hn) ncur[g] = 0ull;
-            if (has_next) {
-                // every earlier term's column-(b+1) word into its group's mask,
-                // four independent loads in flight per thread
+            if (has_next) {  // four independent loads in flight per thread
                 int s = ht;
                 for (; s + 3 * hn < t0; s += 4 * hn) {
                     uint64_t av[4];
@@ -406,27 +449,29 @@ int64_t group_commuting(const paulib_sum* s, int32_t* group, int32_t* offsets, i
     const int64_t nblocks = (m + 63) / 64;
     if (m > INT32_MAX || nblocks > 65535) fail(PAULIB_ERR_UNSUPPORTED, "grouping supports at most 4,194,240 terms");
     StageScope ss(ST_GROUP, st);
-    Scratch at((size_t)anti_col_offset(nblocks) * sizeof(uint64_t), st);
+    // one allocation: the greedy kernel's two result words, then the bit matrix
+    Scratch blockmem(256 + (size_t)anti_col_offset(nblocks) * sizeof(uint64_t), st);
+    int32_t* meta = blockmem.as<int32_t>();
+    uint64_t* atm = reinterpret_cast<uint64_t*>(blockmem.as<char>() + 256);
     {
         const dim3 grid((unsigned)((m + kAntiThreads - 1) / kAntiThreads), (unsigned)nblocks);
         note_launch(ST_GROUP);
-#define L(WPv) k_anticomm<WPv><<<grid, kAntiThreads, 0, st>>>(s->keys, m, at.as<uint64_t>());
+#define L(WPv) k_anticomm<WPv><<<grid, kAntiThreads, 0, st>>>(s->keys, m, atm);
         PAULIB_DISPATCH_WP(s->WP, L);
 #undef L
         check_cuda(cudaGetLastError(), "k_anticomm");
     }
     int rmax = 1;  // smallest row that holds every group m terms can open, plus 64
     while (rmax < kMaxRowWordsPerLane && m + 64 > (int64_t)2048 * rmax) rmax *= 2;
-    Scratch meta(2 * sizeof(int32_t), st);
     std::vector<Scratch> keep;
     keep.reserve(2);
     const int32_t mi = (int32_t)m;
     switch (rmax) {
-        case 1: launch_greedy<1>(at.as<uint64_t>(), mi, group, meta.as<int32_t>(), st, keep); break;
-        case 2: launch_greedy<2>(at.as<uint64_t>(), mi, group, meta.as<int32_t>(), st, keep); break;
-        case 4: launch_greedy<4>(at.as<uint64_t>(), mi, group, meta.as<int32_t>(), st, keep); break;
-        case 8: launch_greedy<8>(at.as<uint64_t>(), mi, group, meta.as<int32_t>(), st, keep); break;
-        default: launch_greedy<16>(at.as<uint64_t>(), mi, group, meta.as<int32_t>(), st, keep); break;
+        case 1: launch_greedy<1>(atm, mi, group, meta, st, keep); break;
+        case 2: launch_greedy<2>(atm, mi, group, meta, st, keep); break;
+        case 4: launch_greedy<4>(atm, mi, group, meta, st, keep); break;
+        case 8: launch_greedy<8>(atm, mi, group, meta, st, keep); break;
+        default: launch_greedy<16>(atm, mi, group, meta, st, keep); break;
     }
     if (offsets || members) {
         // sized for every partition the greedy kernel can return: G <= min(m, 32,704)
@@ -434,11 +479,11 @@ int64_t group_commuting(const paulib_sum* s, int32_t* group, int32_t* offsets, i
         static std::atomic<uint64_t> attr_set{0};
         set_smem_once(k_group_csr, (size_t)(64 * 32 * kMaxRowWordsPerLane - 64) * sizeof(int32_t), attr_set);
         note_launch(ST_GROUP);
-        k_group_csr<<<1, kCsrThreads, smem, st>>>(group, mi, meta.as<int32_t>(), offsets, members);
+        k_group_csr<<<1, kCsrThreads, smem, st>>>(group, mi, meta, offsets, members);
         check_cuda(cudaGetLastError(), "k_group_csr");
     }
     int32_t h[2] = {0, 0};
-    check_cuda(cudaMemcpyAsync(h, meta.p, sizeof(h), cudaMemcpyDeviceToHost, st), "group count");
+    check_cuda(cudaMemcpyAsync(h, meta, sizeof(h), cudaMemcpyDeviceToHost, st), "group count");
     check_cuda(cudaStreamSynchronize(st), "group sync");
     if (h[1]) fail(PAULIB_ERR_UNSUPPORTED, "the partition needs more than 32,704 groups");
     return h[0];

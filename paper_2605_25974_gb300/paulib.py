@@ -337,10 +337,10 @@ def group_commuting(s: "PauliSum", csr: bool = True, stream=None):
     int32 tensors; offsets (G+1,) and members (M,) are None unless csr."""
     import torch
     m = s.n_terms
-    dev = torch.device("cuda", torch.cuda.current_device())
-    group = torch.empty(m, dtype=torch.int32, device=dev)
-    offsets = torch.empty(m + 1, dtype=torch.int32, device=dev) if csr else None
-    members = torch.empty(m, dtype=torch.int32, device=dev) if csr else None
+    buf = torch.empty(3 * m + 1 if csr else m, dtype=torch.int32, device="cuda")  # one allocation
+    group = buf[:m]
+    offsets = buf[m:2 * m + 1] if csr else None
+    members = buf[2 * m + 1:] if csr else None
     ng = _i64(0)
     _check(load().paulib_group_commuting(_vp(s.handle), _vp(_ptr(group)), _vp(_ptr(offsets)), _vp(_ptr(members)),
                                          ctypes.byref(ng), _vp(_stream(stream))))
