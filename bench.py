@@ -399,6 +399,13 @@ def run_ours(args):
     paulib.load()
     if args.coarse_factor > 0:
         paulib.set_tuning(0, args.coarse_factor, 0, 0, 0)
+    gsizes = tuple(int(v) for v in args.grouping_sizes.split(","))
+    if args.only_grouping:
+        # the grouping leg alone (for profiling its kernels); prints its object
+        stream = torch.cuda.current_stream()
+        if rank == 0:
+            print(json.dumps({"grouping": measure_grouping(paulib, stream, max(5, args.steps), gsizes)}), flush=True)
+        return
 
     h = make_workload(args.workload)
     products = h.m * h.m
@@ -587,7 +594,7 @@ def run_ours(args):
 
     grouping = None
     if not args.no_grouping:
-        grouping = measure_grouping(paulib, stream, max(5, args.steps))
+        grouping = measure_grouping(paulib, stream, max(5, args.steps), gsizes)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -623,6 +630,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-products leg")
     ap.add_argument("--no-propagation", action="store_true", help="skip the gate and rotation leg")
     ap.add_argument("--no-grouping", action="store_true", help="skip the commutation-grouping leg")
+    ap.add_argument("--only-grouping", action="store_true", help="run the commutation-grouping leg alone")
+    ap.add_argument("--grouping-sizes", default="200,500,1000,2000,20000",
+                    help="term counts of the grouping leg (comma separated)")
     ap.add_argument("--coarse-factor", type=int, default=0,
                     help="first-level fan-out of the canonicalisation (0: library default); for profiling "
                          "small cases with the range mix of large ones")
