@@ -116,6 +116,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, world, device="cpu"):
+    """The slowest rank's value (the job is as slow as its slowest replica);
+    every rank gets it.  One all-reduce when world > 1."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (ms)."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def make_workload(name):
     from paper_2605_25974_gb300 import workloads as wl
     cfg = WORKLOADS[name]
@@ -455,13 +473,8 @@ def run_ours(args):
     stage_ms, stage_launches = paulib.timing_read(reset=True)
     barrier()
     clk = clocks.stop()
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = products * world / (ms / 1e3)
+    ms = max_over_ranks(statistics.mean(step_ms), world, "cuda")
+    value = job_rate(products, world, ms)
 
     # ---- the same product through one handle (symmetric pairs i <= j)
     for _ in range(2):
@@ -543,7 +556,7 @@ def run_ours(args):
             e2e_ms.append(dt)
         o.close()
         g.close()
-    e2e = statistics.mean(e2e_ms)
+    e2e = max_over_ranks(statistics.mean(e2e_ms), world, "cuda")
     h2d = hx.numel() * 8 + hz.numel() * 8 + hc.numel() * 8
     d2h = (ox.numel() + oz.numel() + oc.numel()) * 8
 
@@ -604,7 +617,7 @@ def run_ours(args):
                        "l2": "512 MiB flush between timed steps"},
             "roofline": roof, "outer_product": outer, "precision": precision, "symmetric": symmetric,
             "batched": batched, "propagation": propagation, "grouping": grouping,
-            "e2e": {"value": products / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_rate(products, world, e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
             "gpu_launches": int(sum(stage_launches.values())),
             "clocks": clk}
