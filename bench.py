@@ -272,19 +272,22 @@ def measure_propagation(paulib, stream, flush, reps, hbm_peak, peak_src, m=8_000
                         "gate_terms_per_s": m * len(gates) / (ms_c / 1e3),
                         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                                      "frac": gbs / hbm_peak, "peak_source": peak_src, "bytes_per_term": per_term}}}
-    # one gate per pass: the HBM-bound case (the same bytes per term)
-    one = [gates[0]]
+    # one gate (H on qubit 137): the one-word kernel, which reads each term's
+    # x and z word of that qubit (two 32-byte sectors) and its phase byte, and
+    # writes only what changes; the compulsory bytes counted are those reads
+    one = [("h", 137, 0)]
 
     def clifford1():
         paulib.apply_clifford(g, one, stream=stream)
         return _NoClose()
 
     ms_1 = timed_events(clifford1, stream, flush, reps)
-    gbs1 = m * per_term / (ms_1 / 1e3) / 1e9
-    res["clifford_single_gate"] = {"ms_per_call": ms_1, "terms_per_s": m / (ms_1 / 1e3),
+    per_term1 = 2 * 32 + 1
+    gbs1 = m * per_term1 / (ms_1 / 1e3) / 1e9
+    res["clifford_single_gate"] = {"gate": "h 137", "ms_per_call": ms_1, "terms_per_s": m / (ms_1 / 1e3),
                                    "roofline": {"bound": "hbm", "achieved": gbs1, "peak": hbm_peak, "unit": "GB/s",
                                                 "frac": gbs1 / hbm_peak, "peak_source": peak_src,
-                                                "bytes_per_term": per_term}}
+                                                "bytes_per_term": per_term1}}
     # rotation: a weight-250 generator anti-commutes with about half the terms
     pb = wl.SumArrays(n, *wl.low_weight_terms(wl.rng_for(602), n, 1, 250), np.ones(1, np.complex128))
     px, pz = pb.x[:, 0], pb.z[:, 0]
@@ -418,6 +421,15 @@ def run_ours(args):
     if args.coarse_factor > 0:
         paulib.set_tuning(0, args.coarse_factor, 0, 0, 0)
     gsizes = tuple(int(v) for v in args.grouping_sizes.split(","))
+    if args.only_propagation:
+        # the gate, rotation and pair-product leg alone (for profiling its kernels)
+        stream = torch.cuda.current_stream()
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+        hbm_peak, peak_src = measured_peaks()
+        res = measure_propagation(paulib, stream, flush, max(3, args.steps), hbm_peak, peak_src)
+        if rank == 0:
+            print(json.dumps({"propagation": res}), flush=True)
+        return
     if args.only_grouping:
         # the grouping leg alone (for profiling its kernels); prints its object
         stream = torch.cuda.current_stream()
@@ -644,6 +656,7 @@ def main():
     ap.add_argument("--no-propagation", action="store_true", help="skip the gate and rotation leg")
     ap.add_argument("--no-grouping", action="store_true", help="skip the commutation-grouping leg")
     ap.add_argument("--only-grouping", action="store_true", help="run the commutation-grouping leg alone")
+    ap.add_argument("--only-propagation", action="store_true", help="run the gate, rotation and pair-product leg alone")
     ap.add_argument("--grouping-sizes", default="200,500,1000,2000,20000",
                     help="term counts of the grouping leg (comma separated)")
     ap.add_argument("--coarse-factor", type=int, default=0,

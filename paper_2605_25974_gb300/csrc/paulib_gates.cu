@@ -20,6 +20,37 @@ namespace paulib {
 
 constexpr int kCliffordThreads = 256;
 
+// One gate's action on the bits of its qubits: (xc, zc) of q1 and (xt, zt) of
+// q2 (zero for one-qubit gates) become (nxc, nzc, nxt, nzt).  Returns the
+// exponent e (mod 4) the image's sign carries in the normal form: the factor
+// i^u from reordering X and Z, times i^{|x&z| - |x'&z'|} over the two qubits.
+__device__ __forceinline__ uint32_t gate_rule(int32_t gate, uint32_t xc, uint32_t zc, uint32_t xt, uint32_t zt,
+                                              uint32_t& nxc, uint32_t& nzc, uint32_t& nxt, uint32_t& nzt) {
+    nxc = xc;
+    nzc = zc;
+    nxt = xt;
+    nzt = zt;
+    uint32_t u = 0;
+    if (gate == PAULIB_GATE_H) {
+        nxc = zc;
+        nzc = xc;
+        u = 2u * (xc & zc);
+    } else if (gate == PAULIB_GATE_S) {
+        nzc = zc ^ xc;
+        u = xc;
+    } else if (gate == PAULIB_GATE_CNOT) {
+        nxt = xt ^ xc;
+        nzc = zc ^ zt;
+    } else {  // CZ
+        nzc = zc ^ xt;
+        nzt = zt ^ xc;
+        u = 2u * (xc & xt);
+    }
+    const uint32_t before = (xc & zc) + (xt & zt);
+    const uint32_t after = (nxc & nzc) + (nxt & nzt);
+    return (u + before - after) & 3u;
+}
+
 // Applies the gate list to one term held in shared memory, word-major (word
 // w of this thread's term at sk[w * kCliffordThreads]), so that a gate reads
 // and writes just the words it touches without bank conflicts; returns the
@@ -38,26 +69,8 @@ __device__ __forceinline__ uint32_t conjugate_term(uint64_t* sk, const int32_t* 
         const bool two = gate == PAULIB_GATE_CNOT || gate == PAULIB_GATE_CZ;
         const uint32_t xc = (uint32_t)(*x1 >> b1) & 1u, zc = (uint32_t)(*z1 >> b1) & 1u;
         const uint32_t xt = two ? (uint32_t)(*x2 >> b2) & 1u : 0u, zt = two ? (uint32_t)(*z2 >> b2) & 1u : 0u;
-        uint32_t nxc = xc, nzc = zc, nxt = xt, nzt = zt;
-        uint32_t u = 0;
-        if (gate == PAULIB_GATE_H) {
-            nxc = zc;
-            nzc = xc;
-            u = 2u * (xc & zc);
-        } else if (gate == PAULIB_GATE_S) {
-            nzc = zc ^ xc;
-            u = xc;
-        } else if (gate == PAULIB_GATE_CNOT) {
-            nxt = xt ^ xc;
-            nzc = zc ^ zt;
-        } else {  // CZ
-            nzc = zc ^ xt;
-            nzt = zt ^ xc;
-            u = 2u * (xc & xt);
-        }
-        const uint32_t before = (xc & zc) + (xt & zt);
-        const uint32_t after = (nxc & nzc) + (nxt & nzt);
-        e = (e + u + before - after) & 3u;
+        uint32_t nxc, nzc, nxt, nzt;
+        e = (e + gate_rule(gate, xc, zc, xt, zt, nxc, nzc, nxt, nzt)) & 3u;
         *x1 ^= (uint64_t)(xc ^ nxc) << b1;
         *z1 ^= (uint64_t)(zc ^ nzc) << b1;
         if (two) {
@@ -95,6 +108,51 @@ __global__ void __launch_bounds__(kCliffordThreads) k_clifford(uint64_t* keys, d
     }
 }
 
+// Gate lists whose qubits all lie in one 64-bit word w (any single gate, for
+// instance): the term's other words do not change, so each term reads and
+// writes only its x and z words w (the struct-of-arrays observation of Sec.
+// III-G, on the per-term key layout), its phase byte, which moves by the change
+// of |x&z| on word w, and its coefficient where the image is -P; a term the
+// gates leave unchanged is only read.
+template <int WP>
+__global__ void __launch_bounds__(kCliffordThreads) k_clifford_word(uint64_t* keys, double2* coef, uint8_t* pbase,
+                                                                    int64_t n, int32_t w,
+                                                                    const int32_t* __restrict__ ops, int32_t nops) {
+    constexpr int NW = 2 * WP;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t* kx = keys + t * NW + w;
+        const uint64_t x0 = kx[0], z0 = kx[WP];
+        uint64_t x = x0, z = z0;
+        const int before = __popcll(x & z);
+        uint32_t e = 0;
+        for (int32_t g = 0; g < nops; ++g) {
+            const int32_t gate = __ldg(ops + 3 * g);
+            const uint32_t b1 = (uint32_t)__ldg(ops + 3 * g + 1) & 63u, b2 = (uint32_t)__ldg(ops + 3 * g + 2) & 63u;
+            const bool two = gate == PAULIB_GATE_CNOT || gate == PAULIB_GATE_CZ;
+            const uint32_t xc = (uint32_t)(x >> b1) & 1u, zc = (uint32_t)(z >> b1) & 1u;
+            const uint32_t xt = two ? (uint32_t)(x >> b2) & 1u : 0u, zt = two ? (uint32_t)(z >> b2) & 1u : 0u;
+            uint32_t nxc, nzc, nxt, nzt;
+            e = (e + gate_rule(gate, xc, zc, xt, zt, nxc, nzc, nxt, nzt)) & 3u;
+            x ^= (uint64_t)(xc ^ nxc) << b1;
+            z ^= (uint64_t)(zc ^ nzc) << b1;
+            if (two) {
+                x ^= (uint64_t)(xt ^ nxt) << b2;
+                z ^= (uint64_t)(zt ^ nzt) << b2;
+            }
+        }
+        if (x != x0 || z != z0) {  // unchanged terms (identity on the gates' qubits) write nothing
+            kx[0] = x;
+            kx[WP] = z;
+            const int after = __popcll(x & z);
+            if (after != before) pbase[t] = (uint8_t)((pbase[t] + after - before) & 3);
+        }
+        if (e) {
+            const double2 c = coef[t];
+            coef[t] = make_double2(-c.x, -c.y);  // e is 2: an exact sign flip
+        }
+    }
+}
+
 void apply_clifford(paulib_sum* s, int32_t nops, const int32_t* ops_host, cudaStream_t st) {
     if (nops == 0 || s->n_terms == 0) return;
     Scratch ops((size_t)nops * 3 * sizeof(int32_t), st);
@@ -106,6 +164,23 @@ void apply_clifford(paulib_sum* s, int32_t nops, const int32_t* ops_host, cudaSt
     const size_t sm = (size_t)2 * s->WP * kCliffordThreads * 8;
     StageScope ss(ST_CONVERT, st);
     note_launch(ST_CONVERT);
+    // one word holding every qubit of the list: touch only that word
+    const int32_t w0 = ops_host[1] >> 6;
+    bool one_word = true;
+    for (int32_t g = 0; g < nops && one_word; ++g) {
+        const int32_t gate = ops_host[3 * g];
+        const bool two = gate == PAULIB_GATE_CNOT || gate == PAULIB_GATE_CZ;
+        one_word = (ops_host[3 * g + 1] >> 6) == w0 && (!two || (ops_host[3 * g + 2] >> 6) == w0);
+    }
+    if (one_word) {
+#define LW(WPv) k_clifford_word<WPv><<<grid, kCliffordThreads, 0, st>>>(s->keys, s->coef, s->pbase, s->n_terms, w0, \
+                                                                        ops.as<int32_t>(), nops);
+        PAULIB_DISPATCH_WP(s->WP, LW);
+#undef LW
+        check_cuda(cudaGetLastError(), "k_clifford_word");
+        s->is_canonical = 0;
+        return;
+    }
 #define L(WPv)                                                                                               \
     {                                                                                                        \
         auto kern = k_clifford<WPv>;                                                                         \

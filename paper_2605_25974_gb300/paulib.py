@@ -337,15 +337,18 @@ def group_commuting(s: "PauliSum", csr: bool = True, stream=None):
     int32 tensors; offsets (G+1,) and members (M,) are None unless csr."""
     import torch
     m = s.n_terms
-    buf = torch.empty(3 * m + 1 if csr else m, dtype=torch.int32, device="cuda")  # one allocation
-    group = buf[:m]
-    offsets = buf[m:2 * m + 1] if csr else None
-    members = buf[2 * m + 1:] if csr else None
+    # one allocation: group of each term, then the offsets, then the members
+    buf = torch.empty(3 * m + 1 if csr else max(m, 1), dtype=torch.int32, device="cuda")
+    p = buf.data_ptr()
     ng = _i64(0)
-    _check(load().paulib_group_commuting(_vp(s.handle), _vp(_ptr(group)), _vp(_ptr(offsets)), _vp(_ptr(members)),
-                                         ctypes.byref(ng), _vp(_stream(stream))))
+    _check(load().paulib_group_commuting(_vp(s.handle), _vp(p), _vp(p + 4 * m if csr else None),
+                                         _vp(p + 4 * (2 * m + 1) if csr else None), ctypes.byref(ng),
+                                         _vp(_stream(stream))))
     g = int(ng.value)
-    return group, g, (offsets[:g + 1] if csr else None), members
+    if not csr:
+        return buf[:m], g, None, None
+    group, offsets, members = torch.split(buf, [m, m + 1, m])
+    return group, g, offsets[:g + 1], members
 
 
 def set_group_candidates(k: int):

@@ -60,6 +60,41 @@ def test_clifford_list_vs_oracle(lib, oracle, n, m, ng):
     assert np.array_equal((c * ik).view(np.uint64), oc.view(np.uint64)) or np.allclose(c * ik, oc, atol=0, rtol=0)
 
 
+ONE_WORD_LISTS = [
+    (500, [("h", 3, 0)]), (500, [("s", 200, 0)]), (500, [("cnot", 130, 191)]), (500, [("cz", 64, 127)]),
+    (500, [("h", 256, 0), ("s", 256, 0), ("cnot", 256, 300), ("cz", 319, 257), ("h", 300, 0), ("s", 319, 0)]),
+    (130, [("s", 129, 0), ("h", 128, 0), ("cnot", 128, 129), ("cz", 129, 128)]),  # the last, partial word
+    (64, [("h", 0, 0), ("cz", 0, 63), ("s", 63, 0), ("cnot", 63, 0)]),
+]
+
+
+@pytest.mark.parametrize("n,gates", ONE_WORD_LISTS)
+def test_clifford_one_word_lists(lib, oracle, n, gates):
+    # every qubit of the list in one 64-bit word: the kernel that reads and
+    # writes only that word, the phase byte and the flipped coefficients.  The
+    # product with a second sum afterwards checks the updated phase bases.
+    rng = np.random.default_rng(n + len(gates))
+    s = random_terms(rng, n, 3000, with_phase=True)
+    b = random_terms(rng, n, 40)
+    with lib.PauliSum.from_arrays(s) as g, lib.PauliSum.from_arrays(b) as gb:
+        lib.apply_clifford(g, gates)
+        x, z, c, k = g.export()
+        with lib.multiply(g, gb, "fp64") as gp:
+            px, pz, pc, _ = gp.export()
+    ox, oz, oc = s.x, s.z, s.c
+    ok = s.k
+    for gate, q1, q2 in gates:
+        ox, oz, oc = oracle.apply_clifford(n, (ox, oz, oc, ok), gate, q1, q2)
+        ok = None
+    assert np.array_equal(x, ox) and np.array_equal(z, oz)
+    ik = np.array([1, 1j, -1, -1j])[k]
+    assert np.array_equal(c * ik, oc)
+    qx, qz, qc, qabs, _ = oracle.multiply_canonical(n, (ox, oz, oc), b.as_tuple())
+    assert np.array_equal(px, qx) and np.array_equal(pz, qz)
+    err = np.maximum(np.abs(pc.real - qc.real), np.abs(pc.imag - qc.imag))
+    assert (err <= TOL64 * qabs).all()
+
+
 def test_clifford_then_compress_is_canonical(lib, oracle):
     rng = np.random.default_rng(5)
     n = 100
