@@ -297,6 +297,18 @@ def measure_propagation(paulib, stream, flush, reps, hbm_peak, peak_src, m=8_000
     ms_r = timed_events(lambda: paulib.rotate(g, px, pz, 0.1, 1e-9), stream, flush, max(2, reps // 2))
     res["rotation"] = {"theta": 0.1, "threshold": 1e-9, "ms_per_step": ms_r, "terms_in": m, "terms_out": int(u),
                        "terms_per_s": m / (ms_r / 1e3)}
+    # the same step on the canonical form of the sum (as in a propagation run,
+    # where every step's input is the previous step's canonical output): only
+    # the partners are sorted, then merged with the already sorted terms
+    cg = paulib.compress(g)
+    out = paulib.rotate(cg, px, pz, 0.1, 1e-9)
+    uc = out.n_terms
+    out.close()
+    ms_rc = timed_events(lambda: paulib.rotate(cg, px, pz, 0.1, 1e-9), stream, flush, max(2, reps // 2))
+    res["rotation_canonical_input"] = {"theta": 0.1, "threshold": 1e-9, "ms_per_step": ms_rc,
+                                       "terms_in": int(cg.n_terms), "terms_out": int(uc),
+                                       "terms_per_s": cg.n_terms / (ms_rc / 1e3)}
+    cg.close()
     # element-wise products of two 8M-term lists (the paper's single multiplication, in bulk)
     xb, zb = wl.low_weight_terms(wl.rng_for(603), n, m, 32)
     gb = paulib.PauliSum.from_arrays(wl.SumArrays(n, xb, zb, wl.coeffs_loguniform(wl.rng_for(604), m)))

@@ -337,6 +337,171 @@ static uint64_t flag_offsets(const uint8_t* flags, uint32_t nch, Scratch& coff, 
     return total;
 }
 
+// ---------------------------------------------------------------- canonical merge
+//
+// A rotation of a canonical sum keeps its terms Q in key order (scaled by
+// cos(theta) where they anti-commute with P); only the partners P Q need
+// sorting.  The partners are canonicalised on their own and the two sorted,
+// duplicate-free lists are merged, a partner equal to some Q adding its
+// coefficient to that Q's: merge-path tiles of kMergeTile outputs.
+
+constexpr int kMergeThreads = 128;
+constexpr int kMergeItems = 4;
+constexpr int kMergeTile = kMergeThreads * kMergeItems;
+constexpr int kMergeCols = kMergeTile + 2;  // the tile's keys plus A[a0-1] and B[b1]
+
+// Keys compared word by word, word 0 most significant: -1, 0 or 1.
+template <int NW>
+__device__ __forceinline__ int key_cmp3(const uint64_t* a, int sa, const uint64_t* b, int sb) {
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        const uint64_t x = a[q * sa], y = b[q * sb];
+        if (x != y) return x < y ? -1 : 1;
+    }
+    return 0;
+}
+
+// split[c] = number of A terms among the first min(L, c * kMergeTile) outputs
+// of the merge (A before B on equal keys).
+template <int WP>
+__global__ void __launch_bounds__(256) k_merge_split(const uint64_t* __restrict__ ak, int64_t na,
+                                                     const uint64_t* __restrict__ bk, int64_t nb, int64_t ntiles,
+                                                     int64_t* split) {
+    constexpr int NW = 2 * WP;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > ntiles) return;
+    const int64_t d = min(na + nb, c * (int64_t)kMergeTile);
+    int64_t lo = max((int64_t)0, d - nb), hi = min(d, na);
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (key_cmp3<NW>(ak + mid * NW, 1, bk + (d - 1 - mid) * NW, 1) <= 0) lo = mid + 1;
+        else hi = mid;
+    }
+    split[c] = lo;
+}
+
+// One tile: stage its keys word-major in shared memory (A[a0-1], A[a0..a1),
+// B[b0..b1), B[b1]), split it again per thread, merge kMergeItems outputs per
+// thread into slot order.  An A term equal to the B term that follows it
+// takes that term's coefficient; the B slot is then left unflagged.  With
+// thr2 > 0, slots whose |c|^2 < thr2 are left unflagged too (truncation).
+template <int WP>
+__global__ void __launch_bounds__(kMergeThreads) k_merge_tile(const uint64_t* __restrict__ ak,
+                                                              const double2* __restrict__ ac, int64_t na,
+                                                              const uint64_t* __restrict__ bk,
+                                                              const double2* __restrict__ bc, int64_t nb,
+                                                              const int64_t* __restrict__ split, double thr2,
+                                                              uint64_t* tk, double2* tc, uint8_t* tflag) {
+    constexpr int NW = 2 * WP;
+    constexpr int S = kMergeCols;
+    extern __shared__ uint64_t s_key[];  // [NW][S]
+    const int64_t L = na + nb;
+    const int64_t d0 = (int64_t)blockIdx.x * kMergeTile, d1 = min(L, d0 + kMergeTile);
+    const int64_t a0 = split[blockIdx.x], a1 = split[blockIdx.x + 1];
+    const int64_t b0 = d0 - a0, b1 = d1 - a1;
+    const int ta = (int)(a1 - a0), tb = (int)(b1 - b0);
+    // staged column j: 0 = A[a0-1], 1..ta = A[a0..a1), ta+1..ta+tb = B[b0..b1), ta+tb+1 = B[b1]
+    for (int e = threadIdx.x; e < (ta + 1) * NW; e += kMergeThreads) {
+        const int j = e / NW, q = e - j * NW;
+        const int64_t ga = a0 - 1 + j;
+        if (ga >= 0 && ga < na) s_key[q * S + j] = __ldg(ak + ga * NW + q);
+    }
+    for (int e = threadIdx.x; e < (tb + 1) * NW; e += kMergeThreads) {
+        const int j = e / NW, q = e - j * NW;
+        const int64_t gb = b0 + j;
+        if (gb < nb) s_key[q * S + ta + 1 + j] = __ldg(bk + gb * NW + q);
+    }
+    __syncthreads();
+    const uint64_t* sA = s_key + 1;       // sA[i], i in [-1, ta)
+    const uint64_t* sB = s_key + ta + 1;  // sB[j], j in [0, tb]
+    const int k = threadIdx.x * kMergeItems;
+    if (d0 + k >= d1) return;
+    int lo = max(0, k - tb), hi = min(k, ta);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (key_cmp3<NW>(sA + mid, S, sB + (k - 1 - mid), S) <= 0) lo = mid + 1;
+        else hi = mid;
+    }
+    int a = lo, b = k - lo;
+    for (int it = 0; it < kMergeItems; ++it) {
+        const int64_t p = d0 + k + it;
+        if (p >= d1) break;
+        const bool takeA = b >= tb || (a < ta && key_cmp3<NW>(sA + a, S, sB + b, S) <= 0);
+        const uint64_t* src;
+        double2 c;
+        bool keep;
+        if (takeA) {
+            src = sA + a;
+            c = ac[a0 + a];
+            // the B term right after it in key order: in the tile, or B[b1]
+            if (b0 + b < nb && key_cmp3<NW>(sA + a, S, sB + b, S) == 0) {
+                const double2 cb = bc[b0 + b];
+                c = make_double2(c.x + cb.x, c.y + cb.y);
+            }
+            keep = true;
+            ++a;
+        } else {
+            src = sB + b;
+            c = bc[b0 + b];
+            // equal to the A term before it: already added there
+            keep = !(a0 + a > 0 && key_cmp3<NW>(sA + a - 1, S, sB + b, S) == 0);
+            ++b;
+        }
+        if (thr2 > 0 && c.x * c.x + c.y * c.y < thr2) keep = false;
+        tflag[p] = keep ? 1 : 0;
+        if (keep) {
+#pragma unroll
+            for (int q = 0; q < NW; ++q) tk[p * NW + q] = src[q * S];
+            tc[p] = c;
+        }
+    }
+}
+
+// Merges the canonical Q part (the first n terms of raw) with the separately
+// canonicalised partners pc into a new canonical sum, truncating at threshold.
+template <int WP>
+static paulib_sum* merge_rotated(const paulib_sum* raw, int64_t n, const paulib_sum* pc, double threshold,
+                                 cudaStream_t st) {
+    constexpr int NW = 2 * WP;
+    const int64_t nb = pc->n_terms, L = n + nb;
+    const int64_t ntiles = (L + kMergeTile - 1) / kMergeTile;
+    Scratch split((size_t)(ntiles + 1) * 8, st);
+    const uint32_t nch = (uint32_t)((L + kChunk - 1) / kChunk);
+    Scratch tkeys((size_t)L * NW * 8, st), tcoef((size_t)L * 16, st), tflag((size_t)nch * kChunk, st), coff;
+    check_cuda(cudaMemsetAsync(tflag.p, 0, (size_t)nch * kChunk, st), "memset flags");
+    {
+        StageScope ss(ST_COMPACT, st);
+        note_launch(ST_COMPACT);
+        k_merge_split<WP><<<(unsigned)((ntiles + 1 + 255) / 256), 256, 0, st>>>(raw->keys, n, pc->keys, nb, ntiles,
+                                                                                split.as<int64_t>());
+        const size_t sm = (size_t)NW * kMergeCols * 8;
+        smem_attr(k_merge_tile<WP>, sm);
+        note_launch(ST_COMPACT);
+        k_merge_tile<WP><<<(unsigned)ntiles, kMergeThreads, sm, st>>>(
+            raw->keys, raw->coef, n, pc->keys, pc->coef, nb, split.as<int64_t>(),
+            threshold > 0 ? threshold * threshold : 0.0, tkeys.as<uint64_t>(), tcoef.as<double2>(),
+            tflag.as<uint8_t>());
+        check_cuda(cudaGetLastError(), "merge kernels");
+    }
+    const uint64_t keep = flag_offsets(tflag.as<uint8_t>(), nch, coff, st);
+    paulib_sum* out = sum_alloc(raw->n_qubits, (int64_t)keep, false, st);
+    out->is_canonical = 1;
+    if (keep > 0) {
+        StageScope ss(ST_COMPACT, st);
+        note_launch(ST_COMPACT);
+        const int sms = device_sm_count();
+        k_compact<WP><<<std::max<uint32_t>(1, std::min<uint32_t>(nch, (uint32_t)sms * 8)), kChunkThreads, 0, st>>>(
+            nch, tflag.as<uint8_t>(), coff.as<uint64_t>(), tkeys.as<uint64_t>(), tcoef.as<double2>(), out->keys,
+            out->coef, out->pbase);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            sum_free(out, st);
+            check_cuda(e, "k_compact");
+        }
+    }
+    return out;
+}
+
 template <int WP>
 static paulib_sum* rotate_wp(const paulib_sum* s, const uint64_t* pk_host, double theta, double threshold, int mode,
                              cudaStream_t st) {
@@ -378,6 +543,32 @@ static paulib_sum* rotate_wp(const paulib_sum* s, const uint64_t* pk_host, doubl
             sum_free(raw, st);
             check_cuda(e, "rotation kernels");
         }
+    }
+    if (s->is_canonical && anti > 0) {
+        // canonical input: the Q part is sorted and duplicate-free already;
+        // canonicalise only the partners (a view of raw's tail), then merge
+        paulib_sum pv = *raw;
+        pv.n_terms = (int64_t)anti;
+        pv.keys = raw->keys + (size_t)n * NW;
+        pv.coef = raw->coef + n;
+        pv.pbase = raw->pbase + n;
+        pv.phase = raw->phase + n;
+        pv.is_canonical = 0;
+        pv.block = nullptr;
+        pv.plan_owned = true;
+        paulib_sum* pc = nullptr;
+        paulib_sum* out = nullptr;
+        try {
+            pc = canon_terms(&pv, mode, st);
+            out = merge_rotated<WP>(raw, n, pc, threshold, st);
+        } catch (...) {
+            if (pc) sum_free(pc, st);
+            sum_free(raw, st);
+            throw;
+        }
+        sum_free(pc, st);
+        sum_free(raw, st);
+        return out;
     }
     paulib_sum* canon = nullptr;
     try {

@@ -141,6 +141,51 @@ def test_rotation_vs_oracle(lib, oracle, n, m, theta, thr):
     assert (err <= TOL64 * np.maximum(oabs, 1e-300)).all(), float(np.max(err / np.maximum(oabs, 1e-300)))
 
 
+@pytest.mark.parametrize("n,m,theta,thr,prec", [(5, 600, 0.4, 0.0, "fp64"), (70, 5000, 1.1, 0.0, "fp64"),
+                                                 (130, 20000, -0.7, 1e-3, "fp64"), (500, 3000, 0.25, 0.0, "fp64"),
+                                                 (1024, 900, 2.0, 0.0, "fp64"), (200, 8000, 0.9, 0.0, "fp32_fp64merge")])
+def test_rotation_of_canonical_sum_merges(lib, oracle, n, m, theta, thr, prec):
+    # a canonical input takes the merge path: the Q part stays sorted, only
+    # the partners P Q are canonicalised, then the two lists are merged.  Half
+    # of the terms are P times other terms, so many partners land on existing
+    # keys; the oracle rotates the raw input directly.
+    from paper_2605_25974_gb300 import workloads as wl
+    rng = np.random.default_rng(7 * n + m)
+    base = random_terms(rng, n, m // 2)
+    p = random_terms(rng, n, 1)
+    px, pz = p.x[:, 0], p.z[:, 0]
+    shifted = wl.SumArrays(n, base.x ^ px[:, None], base.z ^ pz[:, None], wl.coeffs_loguniform(rng, m // 2))
+    both = wl.SumArrays(n, np.concatenate([base.x, shifted.x], 1), np.concatenate([base.z, shifted.z], 1),
+                        np.concatenate([base.c, shifted.c]))
+    with lib.PauliSum.from_arrays(both) as g, lib.compress(g) as cg:
+        assert cg.is_canonical
+        with lib.rotate(cg, px, pz, theta, thr, prec) as r:
+            assert r.is_canonical
+            x, z, c, _ = r.export()
+    ox, oz, oc, oabs, _ = oracle.rotate(n, both.as_tuple(), px, pz, theta, thr)
+    assert np.array_equal(x, ox) and np.array_equal(z, oz)
+    tol = TOL64 if prec == "fp64" else 8 * 2.0 ** -24 * 2
+    err = np.maximum(np.abs(c.real - oc.real), np.abs(c.imag - oc.imag))
+    assert (err <= tol * np.maximum(oabs, 1e-300)).all(), float(np.max(err / np.maximum(oabs, 1e-300)))
+
+
+def test_rotation_of_canonical_sum_tiny_cases(lib, oracle):
+    # one term, every term anti-commuting, and partners landing on other terms
+    from conftest import parse_strings
+    from paper_2605_25974_gb300 import workloads as wl
+    cases = [(["XZ"], "ZI", 0.3), (["XI", "YI", "XZ"], "ZI", 0.8), (["IZ", "XZ", "YZ"], "ZZ", 1.3)]
+    for strs, gen, theta in cases:
+        n, x, z = parse_strings(strs)
+        c = np.arange(1, len(strs) + 1).astype(np.complex128) * (1 + 0.5j)
+        _, gx, gz = parse_strings([gen])
+        s = wl.SumArrays(n, x, z, c)
+        with lib.PauliSum.from_arrays(s) as g, lib.compress(g) as cg, lib.rotate(cg, gx[:, 0], gz[:, 0], theta) as r:
+            rx, rz, rc, _ = r.export()
+        ox, oz, oc, oabs, _ = oracle.rotate(n, s.as_tuple(), gx[:, 0], gz[:, 0], theta)
+        assert np.array_equal(rx, ox) and np.array_equal(rz, oz)
+        assert np.allclose(rc, oc, atol=1e-14, rtol=0)
+
+
 def test_rotation_of_jw_hamiltonian_step(lib, oracle):
     # a propagation step on a Jordan-Wigner-shaped sum: many duplicates merge
     from paper_2605_25974_gb300 import workloads as wl
