@@ -394,6 +394,20 @@ static bool is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Page-locked host memory is mapped into the device's address space: returns
+// the device-side address of such a pointer, or NULL for device or pageable
+// memory.  A kernel can then write there directly over the host link.
+static void* mapped_host_ptr(void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 // Returns a device pointer holding `bytes` of `src` (staging host data).
 static const void* to_device(const void* src, size_t bytes, cudaStream_t s, Scratch& keep) {
     if (!src || bytes == 0) return src;
@@ -501,20 +515,27 @@ paulib_status paulib_sum_export(const paulib_sum* s, uint64_t* x_words, uint64_t
     const size_t wbytes = (size_t)s->W * nt * sizeof(uint64_t);
     const bool dx = is_device_ptr(x_words), dz = is_device_ptr(z_words), dc = is_device_ptr(coeffs);
     const bool dp = phase ? is_device_ptr(phase) : true;
+    // page-locked host outputs are written by the export kernel itself (no
+    // staging copy); pageable ones are staged in device memory and copied
+    void* const mx = dx ? nullptr : mapped_host_ptr(x_words);
+    void* const mz = dz ? nullptr : mapped_host_ptr(z_words);
+    void* const mc = dc ? nullptr : mapped_host_ptr(coeffs);
+    void* const mp = (phase && !dp) ? mapped_host_ptr(phase) : nullptr;
     Scratch sx, sz, sc, sp;
-    uint64_t* tx = x_words;
-    uint64_t* tz = z_words;
-    double* tc = coeffs;
-    uint8_t* tp = phase;
-    if (!dx) { sx = Scratch(wbytes, st); tx = sx.as<uint64_t>(); }
-    if (!dz) { sz = Scratch(wbytes, st); tz = sz.as<uint64_t>(); }
-    if (!dc) { sc = Scratch(nt * 16, st); tc = sc.as<double>(); }
-    if (phase && !dp) { sp = Scratch(nt, st); tp = sp.as<uint8_t>(); }
+    uint64_t* tx = dx ? x_words : static_cast<uint64_t*>(mx);
+    uint64_t* tz = dz ? z_words : static_cast<uint64_t*>(mz);
+    double* tc = dc ? coeffs : static_cast<double*>(mc);
+    uint8_t* tp = dp ? phase : static_cast<uint8_t*>(mp);
+    const bool cx = !tx, cz = !tz, cc = !tc, cp = phase && !tp;
+    if (cx) { sx = Scratch(wbytes, st); tx = sx.as<uint64_t>(); }
+    if (cz) { sz = Scratch(wbytes, st); tz = sz.as<uint64_t>(); }
+    if (cc) { sc = Scratch(nt * 16, st); tc = sc.as<double>(); }
+    if (cp) { sp = Scratch(nt, st); tp = sp.as<uint8_t>(); }
     launch_export(s, tx, tz, tc, tp, st);
-    if (!dx) check_cuda(cudaMemcpyAsync(x_words, tx, wbytes, cudaMemcpyDeviceToHost, st), "export copy");
-    if (!dz) check_cuda(cudaMemcpyAsync(z_words, tz, wbytes, cudaMemcpyDeviceToHost, st), "export copy");
-    if (!dc) check_cuda(cudaMemcpyAsync(coeffs, tc, nt * 16, cudaMemcpyDeviceToHost, st), "export copy");
-    if (phase && !dp) check_cuda(cudaMemcpyAsync(phase, tp, nt, cudaMemcpyDeviceToHost, st), "export copy");
+    if (cx) check_cuda(cudaMemcpyAsync(x_words, tx, wbytes, cudaMemcpyDeviceToHost, st), "export copy");
+    if (cz) check_cuda(cudaMemcpyAsync(z_words, tz, wbytes, cudaMemcpyDeviceToHost, st), "export copy");
+    if (cc) check_cuda(cudaMemcpyAsync(coeffs, tc, nt * 16, cudaMemcpyDeviceToHost, st), "export copy");
+    if (cp) check_cuda(cudaMemcpyAsync(phase, tp, nt, cudaMemcpyDeviceToHost, st), "export copy");
     return PAULIB_OK;
     PAULIB_API_END
 }

@@ -319,3 +319,52 @@ def test_batched_mixed_precision(lib, oracle, mode):
                         tol=fp32_tolerance())
     for s in As + Bs + outs:
         s.close()
+
+
+def test_export_to_pinned_host_memory(lib, oracle):
+    # page-locked host outputs are written by the export kernel directly;
+    # pageable ones go through a device staging copy; both equal the device
+    # export and the oracle
+    import torch
+    from paper_2605_25974_gb300 import workloads as wl
+    h = wl.jw(n=100, m=700, seed=11)
+    with lib.PauliSum.from_arrays(h) as g, lib.multiply(g, g, "fp64") as o:
+        W, U = o.words, o.n_terms
+        dx = torch.empty((W, U), dtype=torch.int64, device="cuda")
+        dz = torch.empty_like(dx)
+        dc = torch.empty((U, 2), dtype=torch.float64, device="cuda")
+        o.export(dx, dz, dc, None)
+        px = torch.empty((W, U), dtype=torch.int64).pin_memory()
+        pz = torch.empty((W, U), dtype=torch.int64).pin_memory()
+        pc = torch.empty((U, 2), dtype=torch.float64).pin_memory()
+        pk = torch.empty(U, dtype=torch.uint8).pin_memory()
+        o.export(px, pz, pc, pk)
+        nx, nz, nc, nk = o.export()
+    torch.cuda.synchronize()
+    assert np.array_equal(px.numpy().view(np.uint64), dx.cpu().numpy().view(np.uint64))
+    assert np.array_equal(pz.numpy().view(np.uint64), nz)
+    assert np.array_equal(pc.numpy().view(np.uint64), dc.cpu().numpy().view(np.uint64))
+    assert np.array_equal(pc.numpy(), np.stack([nc.real, nc.imag], 1)) and not pk.numpy().any()
+    ox, oz, oc, oabs, _ = oracle.multiply_canonical(h.n, h.as_tuple(), h.as_tuple())
+    assert np.array_equal(nx, ox) and np.array_equal(nz, oz)
+
+
+@pytest.mark.parametrize("m", [1000, 1001, 2])
+def test_export_pinned_even_and_odd_counts(lib, m):
+    # page-locked outputs written by the export kernel, even and odd term counts
+    import torch
+    from paper_2605_25974_gb300 import workloads as wl
+    rng = np.random.default_rng(m)
+    x, z = wl.weighted_random(rng, 130, m, 1, 130)
+    s = wl.SumArrays(130, x, z, wl.coeffs_loguniform(rng, m))
+    with lib.PauliSum.from_arrays(s) as g:
+        W = g.words
+        px = torch.empty((W, m), dtype=torch.int64).pin_memory()
+        pz = torch.empty((W, m), dtype=torch.int64).pin_memory()
+        pc = torch.empty((m, 2), dtype=torch.float64).pin_memory()
+        g.export(px, pz, pc, None)
+        nx, nz, nc, _ = g.export()
+    torch.cuda.synchronize()
+    assert np.array_equal(px.numpy().view(np.uint64), nx) and np.array_equal(pz.numpy().view(np.uint64), nz)
+    assert np.array_equal(nx, s.x) and np.array_equal(nz, s.z) and np.array_equal(nc, s.c)
+    assert np.array_equal(pc.numpy()[:, 0], s.c.real) and np.array_equal(pc.numpy()[:, 1], s.c.imag)
