@@ -60,3 +60,23 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert st == 1
     st = lib.paulib_sum_create(10, -1, None, None, None, None, None, ctypes.byref(out))
     assert st == 1
+
+
+def test_gate_rotation_grouping_arguments_rejected_without_gpu(lib):
+    # the NEXT-row entry points check their arguments before any device call
+    lib.paulib_last_error.restype = ctypes.c_char_p
+    for name in ("paulib_apply_clifford", "paulib_rotate", "paulib_multiply_pairwise", "paulib_group_commuting",
+                 "paulib_set_group_candidates"):
+        getattr(lib, name).restype = ctypes.c_int32
+    ng = ctypes.c_int64(-1)
+    assert lib.paulib_group_commuting(None, None, None, None, ctypes.byref(ng), None) == 1
+    assert lib.paulib_apply_clifford(None, 0, None, None) == 1
+    out = ctypes.c_void_p()
+    assert lib.paulib_rotate(None, None, None, ctypes.c_double(0.1), ctypes.c_double(0.0), 0, None,
+                             ctypes.byref(out)) == 1
+    assert lib.paulib_multiply_pairwise(None, None, None, ctypes.byref(out)) == 1
+    # grouping tuning: 1..4 candidates per term
+    assert lib.paulib_set_group_candidates(0) == 1 and b"1..4" in lib.paulib_last_error()
+    assert lib.paulib_set_group_candidates(5) == 1
+    assert lib.paulib_set_group_candidates(2) == 0
+    assert lib.paulib_set_group_candidates(4) == 0
