@@ -98,7 +98,9 @@ paulib_status paulib_sum_info(const paulib_sum* s, int32_t* n_qubits, int64_t* n
 /* Copies a sum out in the paulib_sum_create layout (host or device arrays of
  * at least W*n_terms words / n_terms coefficients).  `phase` may be NULL; a
  * canonical sum has all phases zero.  Stream ordered: host arrays are valid
- * after `stream` is synchronised.                                           */
+ * after `stream` is synchronised.  Page-locked host arrays (cudaHostAlloc,
+ * torch pin_memory) are written by the export kernel directly over the host
+ * link; pageable ones go through a device staging buffer and a copy.        */
 paulib_status paulib_sum_export(const paulib_sum* s, uint64_t* x_words, uint64_t* z_words,
                                 double* coeffs, uint8_t* phase, void* stream);
 
