@@ -61,3 +61,19 @@ def test_batch_sizes():
         assert popcount_rows(a.x | a.z).max() <= 32
     again = wl.batch(problems=20)
     assert np.array_equal(again[2][0].x, probs[2][0].x) and np.array_equal(again[7][1].c, probs[7][1].c)
+
+
+def test_grouping_workload():
+    # random 500-qubit sums: every qubit uniform over {I, X, Y, Z}, distinct
+    # strings, seeded by size
+    for m in (200, 2000):
+        h = wl.grouping(m)
+        assert h.n == 500 and h.m == m and h.x.shape == (8, m)
+        assert len(wl._dedupe(h.x, h.z)) == m
+        assert np.array_equal(h.x, wl.grouping(m).x)
+        assert not (h.x[-1] >> np.uint64(500 - 448)).any() and not (h.z[-1] >> np.uint64(500 - 448)).any()
+        # letters: each of I, X, Y, Z on about a quarter of the qubits
+        xb, zb = wl.unpack_bits(h.x, 500), wl.unpack_bits(h.z, 500)
+        frac = [np.mean(~xb & ~zb), np.mean(xb & ~zb), np.mean(xb & zb), np.mean(~xb & zb)]
+        assert all(abs(f - 0.25) < 0.02 for f in frac)
+    assert not np.array_equal(wl.grouping(200).x[:, :10], wl.grouping(300).x[:, :10])
