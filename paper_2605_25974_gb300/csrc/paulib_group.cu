@@ -21,14 +21,16 @@
 //               per group g, the mask N[g] of the block's terms that
 //               anti-commute with some member of g (the OR of the column-b
 //               words of g's members), transposes the masks into per-term
-//               availability bitsets over groups with warp ballots, and lets
-//               one warp decide the 64 terms in order: a term takes the first
-//               available group (a ballot and a find-first-set over the row),
-//               and the block's later terms that anti-commute with it (a
-//               diagonal matrix word) lose that group.  Meanwhile the other
-//               warps OR the column-(b+1) words of every earlier term into the
-//               masks of block b+1.  Groups can be opened at most 64 per block,
-//               so a row needs the bits of the G groups so far plus 64.
+//               availability rows over groups with warp ballots, and keeps each
+//               term's first few available groups.  One warp then decides the
+//               64 terms in order, a lane per term: a term takes its first
+//               candidate (or new group) not taken by an earlier anti-commuting
+//               term of the block (the diagonal matrix words); its choice is
+//               broadcast with a shuffle and the later terms mark it taken.
+//               Meanwhile the other warps OR the column-(b+1) words of every
+//               earlier term into the masks of block b+1.  At most 64 groups
+//               open per block, so the masks need room for the G groups so far
+//               plus 64.
 //   k_group_csr the members of each group in term order (optional).
 #include <atomic>
 #include <climits>
@@ -75,9 +77,9 @@ __global__ void __launch_bounds__(kAntiThreads) k_anticomm(const uint64_t* __res
 
 // meta[0] receives the number of groups, meta[1] is set when a block would
 // need more than 64 * 32 * RMAX groups.  kc (1..kGroupCands): candidates a
-// term keeps; any value gives the same partition.  MASKS_SMEM / AVAIL_SMEM: the group
-// masks (2 x GC words) and the availability rows (64 x AVS words) live in
-// shared memory, else in the global buffers g_masks / g_avail.
+// term keeps; any value gives the same partition.  MASKS_SMEM / AVAIL_SMEM:
+// the group masks (2 x GC words) and the availability rows (64 x AVS words)
+// live in shared memory, else in the global buffers g_masks / g_avail.
 //
 // Per block: (A1) the masks of the groups opened so far are transposed into
 // one availability row per term; (A2) each row yields the term's first
@@ -150,8 +152,9 @@ __global__ void __launch_bounds__(kGreedyThreads, 1)
         const uint64_t* col = at + anti_col_offset(b);
         if (tid < nb) s_diag[tid] = col[t0 + tid];
         __syncthreads();
-        // (A2) each term's first K available groups: word popcounts, a warp
-        // scan, and the lanes whose words hold candidates K..0 extract them
+        // (A2) each term's first kc available groups (and whether it has more):
+        // word popcounts, a warp scan of them, and the lanes whose words hold
+        // candidates 0..kc-1 extract those bits
         for (int i = warp; i < nb; i += nwarps) {
             int found = 0;
             for (int w0 = 0; w0 < wx && found <= kc; w0 += 32) {
