@@ -579,6 +579,7 @@ __device__ __forceinline__ int prefix_cmp(const uint64_t (&k)[NW], const uint64_
 
 constexpr int kCountThreads = 256;
 constexpr int kCountCols = 64;
+constexpr int kTopBits = 11;  // top-level table of the coarse splitter search: 2^11 + 1 entries
 
 // Coarse splitters are located through a 128-bit window of their keys: all
 // splitters share their first L bits (L is the first position where one of
@@ -631,7 +632,8 @@ __global__ void __launch_bounds__(1024) k_spl_codes(const uint64_t* __restrict__
 template <int NW>
 __device__ __forceinline__ uint32_t locate_coarse(const uint64_t (&k)[NW], const uint64_t* s_c1,
                                                   const uint64_t* s_c2, const uint64_t* p0, uint32_t nsp,
-                                                  uint32_t L, const uint64_t* __restrict__ spl) {
+                                                  uint32_t L, const uint64_t* __restrict__ spl,
+                                                  const uint16_t* s_top) {
     // first L bits against the splitters' shared prefix
     int pc = 0;
 #pragma unroll
@@ -649,7 +651,10 @@ __device__ __forceinline__ uint32_t locate_coarse(const uint64_t (&k)[NW], const
     }
     if (pc) return pc < 0 ? 0u : nsp;
     const uint64_t c1 = reg_bits64<NW>(k, L), c2 = reg_bits64<NW>(k, L + 64u);
-    uint32_t lo = 0, len = nsp;
+    // splitters are ordered by c1 first: those whose top bits of c1 are below
+    // the key's are below it, those above are above it
+    const uint32_t v = (uint32_t)(c1 >> (64 - kTopBits));
+    uint32_t lo = s_top[v], len = (uint32_t)s_top[v + 1] - lo;
     while (len > 0) {
         const uint32_t half = len >> 1, mid = lo + half;
         const uint64_t s1 = s_c1[mid];
@@ -674,7 +679,27 @@ __device__ __forceinline__ uint32_t locate_coarse(const uint64_t (&k)[NW], const
 // then (products) one tile of right-hand keys, then the bucket histogram.
 template <int NW>
 __host__ __device__ constexpr size_t count_smem(uint32_t nsp, bool tile) {
-    return (size_t)nsp * 16 + (size_t)NW * 8 + (tile ? (size_t)kCountCols * NW * 8 : 0) + (size_t)(nsp + 1) * 4;
+    return (size_t)nsp * 16 + (size_t)NW * 8 + (tile ? (size_t)kCountCols * NW * 8 : 0) + (size_t)(nsp + 1) * 4 +
+           (size_t)((1u << kTopBits) + 1) * 2;
+}
+
+// s_top[v] = number of splitters whose code c1 has its top kTopBits bits
+// below v (v = 0 .. 2^kTopBits); c1 is sorted.  Narrows every search to the
+// splitters sharing the key's top bits.
+__device__ __forceinline__ void build_top(const uint64_t* s_c1, uint32_t nsp, uint16_t* s_top) {
+    for (uint32_t v = threadIdx.x; v <= (1u << kTopBits); v += blockDim.x) {
+        uint32_t lo = 0, len = nsp;
+        while (len > 0) {
+            const uint32_t half = len >> 1, mid = lo + half;
+            if ((s_c1[mid] >> (64 - kTopBits)) < v) {
+                lo = mid + 1;
+                len -= half + 1;
+            } else {
+                len = half;
+            }
+        }
+        s_top[v] = (uint16_t)lo;
+    }
 }
 
 // Products: a tile is kCountThreads left terms x kCountCols right terms.
@@ -693,10 +718,13 @@ __global__ void __launch_bounds__(kCountThreads) k_count_prod(ProdSrc<WP, MODE> 
     uint64_t* s_b = s_p0 + NW;
     uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_b + kCountCols * NW);
     const uint32_t nbk = nsp + 1;
+    uint16_t* s_top = reinterpret_cast<uint16_t*>(s_hist + nbk);
     const uint32_t L = meta[0];
     for (uint32_t q = threadIdx.x; q < 2 * nsp; q += blockDim.x) s_c1[q] = codes[q];
     for (uint32_t q = threadIdx.x; q < (uint32_t)NW; q += blockDim.x) s_p0[q] = spl[q];
     for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x) s_hist[q] = 0;
+    __syncthreads();
+    build_top(s_c1, nsp, s_top);  // visible after the tile loop's first barrier
     const uint32_t na = src.na;
     const uint32_t ti_n = (na + kCountThreads - 1) / kCountThreads;
     const uint32_t tj_n = (nb_terms + kCountCols - 1) / kCountCols;
@@ -718,7 +746,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count_prod(ProdSrc<WP, MODE> 
                 const uint64_t* bb = s_b + c * NW;
 #pragma unroll
                 for (int q = 0; q < NW; ++q) k[q] = a[q] ^ bb[q];
-                const uint32_t bkt = locate_coarse<NW>(k, s_c1, s_c2, s_p0, nsp, L, spl);
+                const uint32_t bkt = locate_coarse<NW>(k, s_c1, s_c2, s_p0, nsp, L, spl, s_top);
                 ids[(uint64_t)(j0 + c) * na + i] = (uint16_t)bkt;
                 atomicAdd(&s_hist[bkt], 1u);
             }
@@ -743,15 +771,18 @@ __global__ void __launch_bounds__(kCountThreads) k_count_lin(Src src, uint32_t R
     uint64_t* s_p0 = s_c2 + nsp;
     uint32_t* s_hist = reinterpret_cast<uint32_t*>(s_p0 + NW);
     const uint32_t nbk = nsp + 1;
+    uint16_t* s_top = reinterpret_cast<uint16_t*>(s_hist + nbk);
     const uint32_t L = meta[0];
     for (uint32_t q = threadIdx.x; q < 2 * nsp; q += blockDim.x) s_c1[q] = codes[q];
     for (uint32_t q = threadIdx.x; q < (uint32_t)NW; q += blockDim.x) s_p0[q] = spl[q];
     for (uint32_t q = threadIdx.x; q < nbk; q += blockDim.x) s_hist[q] = 0;
     __syncthreads();
+    build_top(s_c1, nsp, s_top);
+    __syncthreads();
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
         uint64_t k[NW];
         src.key(r, k);
-        const uint32_t bkt = locate_coarse<NW>(k, s_c1, s_c2, s_p0, nsp, L, spl);
+        const uint32_t bkt = locate_coarse<NW>(k, s_c1, s_c2, s_p0, nsp, L, spl, s_top);
         ids[r] = (uint16_t)bkt;
         atomicAdd(&s_hist[bkt], 1u);
     }
