@@ -168,3 +168,69 @@ def test_pairwise_products_vs_kron(oracle):
         lhs = ac[t] * ik[ka[t]] * string_matrix(sa[t]) @ (bc[t] * ik[kb[t]] * string_matrix(sb[t]))
         rhs = oc[t] * ik[ok[t]] * string_matrix(out[t])
         assert np.allclose(lhs, rhs, atol=1e-12, rtol=0)
+
+
+def _apply(oracle, n, s, gates):
+    x, z, c = s
+    for gate, q1, q2 in gates:
+        x, z, c = oracle.apply_clifford(n, (x, z, c), gate, q1, q2)
+    return x, z, c
+
+
+def test_clifford_gate_orders(oracle):
+    # H^2 = S^4 = CNOT^2 = CZ^2 = identity under conjugation; S^2 (= Z up to a
+    # phase) flips the sign of X and Y on its qubit and keeps I and Z
+    rng = np.random.default_rng(17)
+    n = 4
+    strs = ["".join(rng.choice(list(LETTERS), n)) for _ in range(80)]
+    _, x, z = parse_strings(strs)
+    c = rng.standard_normal(len(strs)) + 1j * rng.standard_normal(len(strs))
+    for gates in ([("h", 1, 0)] * 2, [("s", 2, 0)] * 4, [("cnot", 0, 3)] * 2, [("cz", 3, 1)] * 2):
+        ox, oz, oc = _apply(oracle, n, (x, z, c), gates)
+        assert np.array_equal(ox, x) and np.array_equal(oz, z) and np.array_equal(oc, c)
+    ox, oz, oc = _apply(oracle, n, (x, z, c), [("s", 2, 0)] * 2)
+    assert np.array_equal(ox, x) and np.array_equal(oz, z)
+    flip = np.array([s[2] in "XY" for s in strs])
+    assert np.array_equal(oc, np.where(flip, -c, c))
+
+
+def test_rotations_compose_additively(oracle):
+    # U_P(t2) U_P(t1) = U_P(t1 + t2): two steps equal one step by the sum of
+    # the angles; a rotation by -t undoes one by t
+    rng = np.random.default_rng(23)
+    n = 5
+    strs = sorted(set("".join(rng.choice(list(LETTERS), n)) for _ in range(60)))
+    _, x, z = parse_strings(strs)
+    c = rng.standard_normal(len(strs)) + 1j * rng.standard_normal(len(strs))
+    _, px, pz = parse_strings(["XZIYZ"])
+    px, pz = px[:, 0], pz[:, 0]
+    t1, t2 = 0.37, -1.21
+    a = oracle.rotate(n, (x, z, c), px, pz, t1)
+    b = oracle.rotate(n, (a[0], a[1], a[2]), px, pz, t2)
+    one = oracle.rotate(n, (x, z, c), px, pz, t1 + t2)
+    got = dict(zip(format_strings(n, b[0], b[1]), b[2]))
+    want = dict(zip(format_strings(n, one[0], one[1]), one[2]))
+    for s_ in set(got) | set(want):
+        assert abs(got.get(s_, 0) - want.get(s_, 0)) < 1e-12
+    back = oracle.rotate(n, (a[0], a[1], a[2]), px, pz, -t1)
+    got = {s_: v for s_, v in zip(format_strings(n, back[0], back[1]), back[2]) if abs(v) > 1e-12}
+    assert got.keys() == set(strs)
+    for s_, v in zip(strs, c):
+        assert abs(got[s_] - v) < 1e-12
+
+
+def test_pairwise_products_associative_and_involutive(oracle):
+    # (a b) c = a (b c) with phases, and P P = I with phase 0
+    rng = np.random.default_rng(29)
+    n, m = 70, 40
+    sets = [["".join(rng.choice(list(LETTERS), n)) for _ in range(m)] for _ in range(3)]
+    (_, ax, az), (_, bx, bz), (_, cx, cz) = [parse_strings(s) for s in sets]
+    one = np.ones(m, np.complex128)
+    ab = oracle.multiply_pairwise(n, (ax, az, one), (bx, bz, one))
+    ab_c = oracle.multiply_pairwise(n, (ab[0], ab[1], one, ab[3]), (cx, cz, one))
+    bc = oracle.multiply_pairwise(n, (bx, bz, one), (cx, cz, one))
+    a_bc = oracle.multiply_pairwise(n, (ax, az, one), (bc[0], bc[1], one, bc[3]))
+    assert np.array_equal(ab_c[0], a_bc[0]) and np.array_equal(ab_c[1], a_bc[1])
+    assert np.array_equal(ab_c[3], a_bc[3])
+    sq = oracle.multiply_pairwise(n, (ax, az, one), (ax, az, one))
+    assert not sq[0].any() and not sq[1].any() and not sq[3].any()
