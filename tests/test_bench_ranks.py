@@ -3,7 +3,8 @@ groups on the CPU.  The product is replicated per GPU (nothing is sharded);
 what N > 1 adds is rank discovery from the torchrun environment, the
 max-over-ranks step time every rank agrees on, the whole-job rate (units of
 all ranks over the slowest rank's time), and the reference arm that runs on
-rank 0 only."""
+rank 0 only.  The reference arm's JSON line is checked too: it runs the CPU
+oracle and needs no GPU."""
 import os
 import socket
 import sys
@@ -72,3 +73,25 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     args = argparse.Namespace(workload="tiny", steps=1, warmup=0, gpus=2)
     assert bench.run_reference(args) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_one_contract_line():
+    # the reference arm (the CPU oracle, timed on the host) runs without a GPU
+    # and prints one JSON line with the keys the benchmark contract names
+    import json
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "jw_hh_n100_m2000",
+                          "--steps", "1", "--warmup", "0"], cwd=root, env=env, capture_output=True, text=True,
+                         timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "products/s" and d["value"] > 0
+    assert d["steps"] == 1 and d["warmup"] == 0 and d["higher_is_better"] is True
+    assert d["config"]["workload"] == "jw_hh_n100_m2000"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
