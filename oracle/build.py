@@ -18,7 +18,7 @@ def build_oracle(force: bool = False) -> str:
         return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           SRC, "-o", tmp]
+           SRC, "-o", tmp, "-pthread"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB

@@ -31,6 +31,7 @@ def _load():
         lib = ctypes.CDLL(build_oracle())
         lib.oracle_string_product.restype = ctypes.c_int
         lib.oracle_multiply_canonical.restype = ctypes.c_void_p
+        lib.oracle_multiply_canonical_range.restype = ctypes.c_void_p
         lib.oracle_compress.restype = ctypes.c_void_p
         lib.oracle_result_size.restype = ctypes.c_int64
         lib.oracle_result_size.argtypes = [ctypes.c_void_p]
@@ -130,6 +131,24 @@ def multiply_canonical(n, a, b):
                                       _p(ac, _f64p), _p(ak, _u8p), ctypes.c_int64(nb), _p(bx, _u64p),
                                       _p(bz, _u64p), _p(bc, _f64p), _p(bk, _u8p))
     return _take(ctypes.c_void_p(h), _words(n))
+
+
+def multiply_canonical_range(n, a, b, lo=None, hi=None, threads=1):
+    """Terms of the canonical product A*B whose key lies in [lo, hi), computed
+    with ``threads`` host threads.  lo/hi are 2W-word keys (x words then z
+    words) or None for an open end.  Returns (x, z, c, abs_sum, count) as
+    multiply_canonical does; consecutive ranges concatenate to the whole sum."""
+    lib = _load()
+    ax, az, ac, ak, na = _prep(n, *a[:3], a[3] if len(a) > 3 else None)
+    bx, bz, bc, bk, nb = _prep(n, *b[:3], b[3] if len(b) > 3 else None)
+    W = _words(n)
+    lo_a = None if lo is None else np.ascontiguousarray(np.asarray(lo, dtype=np.uint64).reshape(2 * W))
+    hi_a = None if hi is None else np.ascontiguousarray(np.asarray(hi, dtype=np.uint64).reshape(2 * W))
+    h = lib.oracle_multiply_canonical_range(int(n), ctypes.c_int64(na), _p(ax, _u64p), _p(az, _u64p),
+                                            _p(ac, _f64p), _p(ak, _u8p), ctypes.c_int64(nb), _p(bx, _u64p),
+                                            _p(bz, _u64p), _p(bc, _f64p), _p(bk, _u8p), _p(lo_a, _u64p),
+                                            _p(hi_a, _u64p), int(threads))
+    return _take(ctypes.c_void_p(h), W)
 
 
 def compress(n, s):

@@ -42,7 +42,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <cmath>
+#include <algorithm>
 #include <map>
+#include <thread>
 #include <vector>
 
 namespace {
@@ -261,6 +263,129 @@ void* oracle_compress(int n, int64_t nt, const uint64_t* xs, const uint64_t* zs,
     }
     Result* r = new Result; r->n = n; r->W = W;
     emit(m, r);
+    return r;
+}
+
+// Canonical product restricted to the key range [lo, hi) (lo or hi NULL:
+// open at that end), with the right-hand terms split into nthreads contiguous
+// blocks, one std::thread each.  Used to check full-size products one key range
+// at a time, so host memory stays bounded: the results of consecutive ranges,
+// concatenated, are the canonical sum.
+//
+// A pair is selected by the word-wise XOR of its factors' keys (the key of a
+// product string; tests/test_oracle_pins.py pins the key set {a_i XOR b_j}
+// against Kronecker matrices).  Each selected pair is then multiplied qubit by
+// qubit from the letter table exactly as in oracle_multiply_canonical, and its
+// letter-table key must equal the XOR (else the call aborts).  Sort and
+// combine (Sec. III-H) is done literally: every thread lists its selected
+// products (key, pair, coefficient), sorts the list by (key, j, i), and the
+// sorted lists are merged in key order; equal keys are summed with Neumaier's
+// compensated sum in (j, i) order, so the result does not depend on thread
+// timing.
+namespace {
+struct RangeRec { int64_t j, i; double re, im, abs; };
+struct RangeList {
+    int W2 = 0;
+    std::vector<uint64_t> keys;   // W2 words per record
+    std::vector<RangeRec> recs;
+    std::vector<int64_t> order;   // records sorted by (key, j, i)
+    bool less(int64_t p, int64_t q) const {
+        const uint64_t* a = &keys[(size_t)p * W2];
+        const uint64_t* b = &keys[(size_t)q * W2];
+        for (int w = 0; w < W2; ++w)
+            if (a[w] != b[w]) return a[w] < b[w];
+        if (recs[p].j != recs[q].j) return recs[p].j < recs[q].j;
+        return recs[p].i < recs[q].i;
+    }
+};
+}  // namespace
+
+void* oracle_multiply_canonical_range(int n, int64_t na, const uint64_t* ax, const uint64_t* az,
+                                      const double* ac, const uint8_t* ka, int64_t nb, const uint64_t* bx,
+                                      const uint64_t* bz, const double* bc, const uint8_t* kb,
+                                      const uint64_t* lo, const uint64_t* hi, int nthreads) {
+    const int W = words_for(n);
+    if (nthreads < 1) nthreads = 1;
+    std::vector<uint64_t> klo, khi;
+    if (lo) klo.assign(lo, lo + 2 * W);
+    if (hi) khi.assign(hi, hi + 2 * W);
+    std::vector<Str> as;
+    as.reserve(na);
+    for (int64_t i = 0; i < na; ++i) as.push_back(load_term(W, na, ax, az, i));
+    std::vector<RangeList> lists(nthreads);
+    auto work = [&](int t) {
+        const int64_t j0 = nb * t / nthreads, j1 = nb * (t + 1) / nthreads;
+        RangeList& L = lists[t];
+        L.W2 = 2 * W;
+        std::vector<uint64_t> kx(2 * W);
+        Str o;
+        for (int64_t j = j0; j < j1; ++j) {
+            Str b = load_term(W, nb, bx, bz, j);
+            Cplx cb = load_coef(bc, j);
+            for (int64_t i = 0; i < na; ++i) {
+                for (int w = 0; w < W; ++w) {
+                    kx[w] = as[i].x[w] ^ b.x[w];
+                    kx[W + w] = as[i].z[w] ^ b.z[w];
+                }
+                if (lo && kx < klo) continue;
+                if (hi && !(kx < khi)) continue;
+                int k = string_product(n, as[i], b, &o);
+                for (int w = 0; w < W; ++w)
+                    if (o.x[w] != kx[w] || o.z[w] != kx[W + w]) std::abort();
+                k = (k + (ka ? ka[i] : 0) + (kb ? kb[j] : 0)) % 4;
+                Cplx ca = load_coef(ac, i);
+                Cplx c = rot(cmul(ca, cb), k);
+                L.keys.insert(L.keys.end(), kx.begin(), kx.end());
+                L.recs.push_back(RangeRec{j, i, c.re, c.im, std::hypot(ca.re, ca.im) * std::hypot(cb.re, cb.im)});
+            }
+        }
+        L.order.resize(L.recs.size());
+        for (size_t q = 0; q < L.order.size(); ++q) L.order[q] = (int64_t)q;
+        std::sort(L.order.begin(), L.order.end(), [&L](int64_t p, int64_t q) { return L.less(p, q); });
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nthreads; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto& th : pool) th.join();
+    // merge the sorted lists in key order (threads hold disjoint j blocks in
+    // increasing order, so among equal keys the lower thread comes first)
+    Result* r = new Result; r->n = n; r->W = W;
+    std::vector<size_t> cur(nthreads, 0);
+    const uint64_t* last = nullptr;
+    Acc acc;
+    auto flush = [&]() {
+        if (!last) return;
+        r->keys.emplace_back(last, last + 2 * W);
+        r->coef.push_back(acc.re.value());
+        r->coef.push_back(acc.im.value());
+        r->abs_sum.push_back(acc.abs_sum);
+        r->count.push_back(acc.count);
+        acc = Acc();
+    };
+    for (;;) {
+        int best = -1;
+        const uint64_t* bk = nullptr;
+        for (int t = 0; t < nthreads; ++t) {
+            if (cur[t] >= lists[t].order.size()) continue;
+            const uint64_t* k = &lists[t].keys[(size_t)lists[t].order[cur[t]] * 2 * W];
+            if (best < 0 || std::lexicographical_compare(k, k + 2 * W, bk, bk + 2 * W)) {
+                best = t;
+                bk = k;
+            }
+        }
+        if (best < 0) break;
+        const RangeRec& rec = lists[best].recs[(size_t)lists[best].order[cur[best]]];
+        if (!last || !std::equal(bk, bk + 2 * W, last)) {
+            flush();
+            last = bk;
+        }
+        acc.re.add(rec.re);
+        acc.im.add(rec.im);
+        acc.abs_sum += rec.abs;
+        acc.count += 1;
+        ++cur[best];
+    }
+    flush();
     return r;
 }
 

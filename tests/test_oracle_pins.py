@@ -305,3 +305,62 @@ def test_compensated_sum_vs_correctly_rounded_sum(oracle):
         for t in v:
             naive += t
     assert oracle.compensated_sum(np.array([1e16, 1.0, -1e16])) == 1.0
+
+
+def _sample_bounds(n, a, b, nsamp, nranges, seed):
+    """Sorted distinct keys of sampled product pairs (numpy XOR of the words),
+    spaced to cut the key space into about ``nranges`` ranges."""
+    rng = np.random.default_rng(seed)
+    ia = rng.integers(0, a.m, nsamp)
+    jb = rng.integers(0, b.m, nsamp)
+    k = np.concatenate([a.x[:, ia] ^ b.x[:, jb], a.z[:, ia] ^ b.z[:, jb]], axis=0).T
+    k = np.unique(k, axis=0)  # lexicographic rows, word 0 first
+    step = max(1, len(k) // nranges)
+    return [k[q] for q in range(step, len(k), step)]
+
+
+@pytest.mark.parametrize("n,ma,mb,threads", [(20, 200, 150, 3), (130, 120, 90, 4), (64, 300, 1, 2), (5, 40, 40, 5)])
+def test_range_mode_concatenates_to_plain_mode(oracle, n, ma, mb, threads):
+    # The key-range, threaded canonical product (used for full-size checks)
+    # against the plain ordered-map mode: consecutive ranges concatenated give
+    # the same keys, counts and |contribution| sums, and coefficients equal up
+    # to compensated-summation rounding.
+    from paper_2605_25974_gb300 import workloads as wl
+    rng = wl.rng_for(900 + n)
+    ax, az = wl.weighted_random(rng, n, ma, 1, min(n, 12))
+    bx, bz = wl.weighted_random(rng, n, mb, 1, min(n, 12))
+    a = wl.SumArrays(n, ax, az, wl.coeffs_normal(rng, ma), rng.integers(0, 4, ma).astype(np.uint8))
+    b = wl.SumArrays(n, bx, bz, wl.coeffs_normal(rng, mb), rng.integers(0, 4, mb).astype(np.uint8))
+    full = oracle.multiply_canonical(n, a.as_tuple(), b.as_tuple())
+    bounds = _sample_bounds(n, a, b, 2000, 6, n)
+    edges = [None] + bounds + [None]
+    parts = [oracle.multiply_canonical_range(n, a.as_tuple(), b.as_tuple(), lo, hi, threads)
+             for lo, hi in zip(edges[:-1], edges[1:])]
+    cat = [np.concatenate([p[q] for p in parts], axis=-1) for q in range(5)]
+    assert np.array_equal(cat[0], full[0]) and np.array_equal(cat[1], full[1])
+    assert np.array_equal(cat[4], full[4])
+    assert np.allclose(cat[3], full[3], rtol=1e-15, atol=0)
+    err = np.maximum(np.abs(cat[2].real - full[2].real), np.abs(cat[2].imag - full[2].imag))
+    assert np.all(err <= 1e-15 * full[3])
+    # an empty range and a single-key range
+    k0 = np.concatenate([full[0][:, 0], full[1][:, 0]])
+    e = oracle.multiply_canonical_range(n, a.as_tuple(), b.as_tuple(), k0, k0, threads)
+    assert e[0].shape[1] == 0
+    k1 = np.concatenate([full[0][:, 1], full[1][:, 1]])
+    one = oracle.multiply_canonical_range(n, a.as_tuple(), b.as_tuple(), k0, k1, threads)
+    assert one[0].shape[1] == 1 and one[4][0] == full[4][0]
+
+
+def test_range_mode_jw_hh_heavy_identity(oracle):
+    from paper_2605_25974_gb300 import workloads as wl
+    h = wl.jw(n=40, m=300, seed=11)
+    full = oracle.multiply_canonical(h.n, h.as_tuple(), h.as_tuple())
+    bounds = _sample_bounds(h.n, h, h, 5000, 9, 3)
+    edges = [None] + bounds + [None]
+    parts = [oracle.multiply_canonical_range(h.n, h.as_tuple(), h.as_tuple(), lo, hi, 4)
+             for lo, hi in zip(edges[:-1], edges[1:])]
+    x = np.concatenate([p[0] for p in parts], axis=1)
+    cnt = np.concatenate([p[4] for p in parts])
+    c = np.concatenate([p[2] for p in parts])
+    assert np.array_equal(x, full[0]) and np.array_equal(cnt, full[4]) and cnt.max() == 300
+    assert np.all(np.abs(c - full[2]) <= 1e-15 * full[3])
