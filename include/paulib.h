@@ -95,6 +95,14 @@ paulib_status paulib_sum_create(int32_t n_qubits, int64_t n_terms, const uint64_
 paulib_status paulib_sum_info(const paulib_sum* s, int32_t* n_qubits, int64_t* n_terms,
                               int32_t* is_canonical);
 
+/* Export of terms [first, first + count) of a sum, with the layout and
+ * rules of paulib_sum_export for a sum of `count` terms (arrays hold W*count
+ * words, count coefficients, count phase bytes).  Lets a caller stream a
+ * large sum out in slices.  No counterpart in the paper.
+ * Errors: INVALID_ARG (NULL sum or outputs, a range outside the sum), CUDA. */
+paulib_status paulib_sum_export_range(const paulib_sum* s, int64_t first, int64_t count, uint64_t* x_words,
+                                      uint64_t* z_words, double* coeffs, uint8_t* phase, void* stream);
+
 /* Copies a sum out in the paulib_sum_create layout (host or device arrays of
  * at least W*n_terms words / n_terms coefficients).  `phase` may be NULL; a
  * canonical sum has all phases zero.  Stream ordered: host arrays are valid
@@ -217,6 +225,44 @@ paulib_status paulib_multiply_noalloc(int32_t n_qubits, int64_t na, const uint64
 paulib_status paulib_set_tuning(int32_t key_words, int32_t coarse_factor, int32_t oversample,
                                 int32_t count_ctas_per_sm, int32_t range_ctas_per_sm);
 
+/* Canonicalisation method (no counterpart in the paper; results never
+ * depend on it, up to the summation order of equal keys).
+ *   method 1 (default): range sort.  Records stay 32-bit pair numbers, keys
+ *     are recomputed from the factors in every pass, and the merged terms are
+ *     compacted into an output sized exactly.
+ *   method 0: slot sort.  Each record's term (key, and coefficient with i^k
+ *     folded in) is formed once into a fine key range; runs of ranges are
+ *     ordered in shared memory and merged straight into the output sum, whose
+ *     storage is sized for one term per record (|A|*|B|, or |A|(|A|+1)/2
+ *     when both operands are the same sum) and trimmed only in its term
+ *     count.  It hands a call to the range sort when a device check fails
+ *     (see paulib_last_canon_method).
+ * leaf_cap: terms per slot-sort leaf (16..4096, at most the compiled
+ * capacity: 1024 up to four key words per half, 8192/(2*WP) beyond);
+ * slot_target: mean terms per fine range; slot_oversample: sample keys per
+ * fine range.  method -1 keeps the method; for the other arguments -1 keeps
+ * a setting and 0 restores its default.  Applies to keys of `key_words`
+ * words (0 = every size).
+ * Errors: INVALID_ARG for values outside these ranges.                      */
+paulib_status paulib_set_slot_tuning(int32_t key_words, int32_t method, int32_t leaf_cap, int32_t slot_target,
+                                     int32_t slot_oversample);
+
+/* Which method produced the calling thread's last canonical product or
+ * compress result: *method = 0 slot sort, 1 range sort, -1 none yet;
+ * *fallback_bits = the device check bits that made the slot sort hand the
+ * call to the range sort (64: an oversized range whose output could reach
+ * its own terms, 128: a sub-range above a leaf, 256: a bounded wait expired,
+ * 1024/2048: a leaf's or a sample's whole-key order check failed, which needs
+ * a 64-bit key-hash collision), 0 otherwise.
+ * Errors: INVALID_ARG for NULL pointers.                                    */
+paulib_status paulib_last_canon_method(int32_t* method, int32_t* fallback_bits);
+
+/* Shape of the calling thread's last slot sort, for tuning: stats[0] coarse
+ * ranges, [1] slot capacity per range, [2] leaves, [3] terms per leaf (the
+ * capacity), [4] mean terms per slot aimed at.  All zero before the first
+ * slot sort.  No counterpart in the paper.  Errors: INVALID_ARG (NULL).      */
+paulib_status paulib_last_canon_stats(int64_t* stats);
+
 /* Element-wise products: output term t = a_t * b_t, the paper's single
  * Pauli-string multiplication (Sec. III-A, III-E) applied to |a| pairs at
  * once.  Requires |a| == |b| and equal qubit counts.  The output is a new raw
@@ -303,13 +349,15 @@ paulib_status paulib_set_group_candidates(int32_t k);
  *   0 input conversion, 1 splitter sampling and selection, 2 coarse count,
  *   3 coarse scatter, 4 range splitting (the per-range worklist kernel),
  *   5 output compaction, 6 raw outer product, 7 export, 8 leaf sort + merge,
- *   9 commutation grouping.
+ *   9 commutation grouping, 10 fine splitting of the slot sort (sample,
+ *   splitters, locating every record), 11 slot offsets, leaf packing and
+ *   term placement of the slot sort.
  * paulib_timing_enable(1) starts recording (0 stops).  paulib_timing_read
  * waits for recorded events, adds their times to ms[PAULIB_STAGES] and the
  * launch counts to launches[PAULIB_STAGES] (either may be NULL), and clears
  * the totals when `reset` is nonzero.  Launch counts are kept even when
  * event timing is off.                                                      */
-#define PAULIB_STAGES 10
+#define PAULIB_STAGES 12
 paulib_status paulib_timing_enable(int32_t on);
 paulib_status paulib_timing_read(double* ms, int64_t* launches, int32_t reset);
 

@@ -344,6 +344,62 @@ void set_tuning(int key_words, const Tuning& t) {
     set_tuning_locked(key_words, t);
 }
 
+namespace {
+std::mutex g_slot_mu;
+SlotTuning g_slot_all;
+std::vector<std::pair<int, SlotTuning>> g_slot_by_words;
+thread_local int g_canon_method = -1;
+thread_local int g_canon_bits = 0;
+}  // namespace
+
+SlotTuning slot_tuning_for(int key_words) {
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    for (const auto& kv : g_slot_by_words)
+        if (kv.first == key_words) return kv.second;
+    return g_slot_all;
+}
+
+void set_slot_tuning(int key_words, const SlotTuning& t, bool) {
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    if (key_words <= 0) {
+        g_slot_all = t;
+        g_slot_by_words.clear();
+        return;
+    }
+    for (auto& kv : g_slot_by_words)
+        if (kv.first == key_words) {
+            kv.second = t;
+            return;
+        }
+    g_slot_by_words.push_back({key_words, t});
+}
+
+void note_canon_method(int method, int bits) {
+    g_canon_method = method;
+    g_canon_bits = bits;
+}
+
+int last_canon_method(int* bits) {
+    *bits = g_canon_bits;
+    return g_canon_method;
+}
+
+namespace {
+thread_local int64_t g_canon_stats[5] = {0, 0, 0, 0, 0};
+}
+
+void note_canon_stats(int64_t ranges, int64_t slots_per_range, int64_t leaves, int64_t leaf_cap, int64_t target) {
+    g_canon_stats[0] = ranges;
+    g_canon_stats[1] = slots_per_range;
+    g_canon_stats[2] = leaves;
+    g_canon_stats[3] = leaf_cap;
+    g_canon_stats[4] = target;
+}
+
+void last_canon_stats(int64_t* out5) {
+    for (int q = 0; q < 5; ++q) out5[q] = g_canon_stats[q];
+}
+
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 paulib_sum* sum_alloc(int32_t n_qubits, int64_t n_terms, bool with_phase, cudaStream_t s) {
@@ -504,11 +560,41 @@ paulib_status paulib_sum_info(const paulib_sum* s, int32_t* n_qubits, int64_t* n
     PAULIB_API_END
 }
 
+static void export_impl(const paulib_sum* s, uint64_t* x_words, uint64_t* z_words, double* coeffs,
+                        uint8_t* phase, void* stream);
+
 paulib_status paulib_sum_export(const paulib_sum* s, uint64_t* x_words, uint64_t* z_words,
                                 double* coeffs, uint8_t* phase, void* stream) {
     PAULIB_API_BEGIN
     if (!s) fail(PAULIB_ERR_INVALID_ARG, "sum is NULL");
-    if (s->n_terms == 0) return PAULIB_OK;
+    export_impl(s, x_words, z_words, coeffs, phase, stream);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_sum_export_range(const paulib_sum* s, int64_t first, int64_t count, uint64_t* x_words,
+                                      uint64_t* z_words, double* coeffs, uint8_t* phase, void* stream) {
+    PAULIB_API_BEGIN
+    if (!s) fail(PAULIB_ERR_INVALID_ARG, "sum is NULL");
+    if (first < 0 || count < 0 || first > s->n_terms || count > s->n_terms - first)
+        fail(PAULIB_ERR_INVALID_ARG, "terms [" + std::to_string(first) + ", " + std::to_string(first + count) +
+                                         ") are outside the sum's " + std::to_string(s->n_terms) + " terms");
+    paulib_sum v = *s;  // a view of terms [first, first + count): no ownership
+    v.n_terms = count;
+    if (count > 0) {
+        v.keys = s->keys + (size_t)first * 2 * s->WP;
+        v.coef = s->coef + first;
+        v.pbase = s->pbase + first;
+        v.phase = s->phase ? s->phase + first : nullptr;
+    }
+    export_impl(&v, x_words, z_words, coeffs, phase, stream);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+static void export_impl(const paulib_sum* s, uint64_t* x_words, uint64_t* z_words, double* coeffs,
+                        uint8_t* phase, void* stream) {
+    if (s->n_terms == 0) return;
     if (!x_words || !z_words || !coeffs) fail(PAULIB_ERR_INVALID_ARG, "output arrays must be non-NULL");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nt = (size_t)s->n_terms;
@@ -536,8 +622,6 @@ paulib_status paulib_sum_export(const paulib_sum* s, uint64_t* x_words, uint64_t
     if (cz) check_cuda(cudaMemcpyAsync(z_words, tz, wbytes, cudaMemcpyDeviceToHost, st), "export copy");
     if (cc) check_cuda(cudaMemcpyAsync(coeffs, tc, nt * 16, cudaMemcpyDeviceToHost, st), "export copy");
     if (cp) check_cuda(cudaMemcpyAsync(phase, tp, nt, cudaMemcpyDeviceToHost, st), "export copy");
-    return PAULIB_OK;
-    PAULIB_API_END
 }
 
 void paulib_sum_destroy(paulib_sum* s) {
@@ -761,6 +845,42 @@ paulib_status paulib_set_tuning(int32_t key_words, int32_t coarse_factor, int32_
                                 int32_t count_ctas_per_sm, int32_t range_ctas_per_sm) {
     PAULIB_API_BEGIN
     set_tuning(key_words, Tuning{coarse_factor, oversample, count_ctas_per_sm, range_ctas_per_sm});
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_set_slot_tuning(int32_t key_words, int32_t method, int32_t leaf_cap, int32_t slot_target,
+                                     int32_t slot_oversample) {
+    PAULIB_API_BEGIN
+    if (method < -1 || method > 1) fail(PAULIB_ERR_INVALID_ARG, "method must be -1, 0 or 1");
+    if (leaf_cap < -1 || (leaf_cap > 0 && (leaf_cap < 16 || leaf_cap > 4096)))
+        fail(PAULIB_ERR_INVALID_ARG, "leaf_cap must be -1, 0 or 16..4096");
+    if (slot_target < -1 || slot_target > (1 << 20)) fail(PAULIB_ERR_INVALID_ARG, "slot_target must be -1..2^20");
+    if (slot_oversample < -1 || slot_oversample > 64) fail(PAULIB_ERR_INVALID_ARG, "slot_oversample must be -1..64");
+    SlotTuning t = slot_tuning_for(key_words > 0 ? key_words : -1);
+    if (method >= 0) t.method = method;
+    if (leaf_cap >= 0) t.leaf_cap = leaf_cap;
+    if (slot_target >= 0) t.target = slot_target;
+    if (slot_oversample >= 0) t.oversample = slot_oversample;
+    set_slot_tuning(key_words, t, true);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_last_canon_stats(int64_t* stats) {
+    PAULIB_API_BEGIN
+    if (!stats) fail(PAULIB_ERR_INVALID_ARG, "NULL argument");
+    last_canon_stats(stats);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_last_canon_method(int32_t* method, int32_t* fallback_bits) {
+    PAULIB_API_BEGIN
+    if (!method || !fallback_bits) fail(PAULIB_ERR_INVALID_ARG, "NULL argument");
+    int bits = 0;
+    *method = last_canon_method(&bits);
+    *fallback_bits = bits;
     return PAULIB_OK;
     PAULIB_API_END
 }

@@ -1,7 +1,7 @@
 // paulib_canon.cu -- canonical product of two sums (paulib_multiply with
 // PAULIB_OUT_CANONICAL) and the allocation-free variant; the pipeline itself
 // is in paulib_pipeline.cuh.
-#include "paulib_pipeline.cuh"
+#include "paulib_slots.cuh"
 
 namespace paulib {
 

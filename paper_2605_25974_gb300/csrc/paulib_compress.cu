@@ -1,6 +1,6 @@
 // paulib_compress.cu -- canonical form of one sum (paulib_compress,
 // PauLIB Sec. III-H sort_and_combine); the pipeline is in paulib_pipeline.cuh.
-#include "paulib_pipeline.cuh"
+#include "paulib_slots.cuh"
 
 namespace paulib {
 

@@ -91,6 +91,26 @@ struct Tuning {
 Tuning tuning_for(int key_words);
 void set_tuning(int key_words, const Tuning& t);
 
+// Canonicalisation method and slot-sort tuning (paulib_set_slot_tuning);
+// never changes results.  0 fields mean the built-in default.
+struct SlotTuning {
+    int method = 1;      // 0 slot sort, 1 range sort (the default: faster on every workload measured)
+    int leaf_cap = 0;    // terms per leaf (at most the compiled capacity)
+    int target = 0;      // mean terms per fine slot
+    int oversample = 0;  // sample keys per fine slot
+};
+SlotTuning slot_tuning_for(int key_words);
+void set_slot_tuning(int key_words, const SlotTuning& t, bool keep_method);
+// Records which method produced the last canonical result on this thread
+// (0 slot sort, 1 range sort) and the device bits that made the slot sort
+// hand the case over (0 when it did not).
+void note_canon_method(int method, int bits);
+int last_canon_method(int* bits);
+// Shape of the last slot sort on this thread: coarse ranges, slot capacity
+// per range, leaves, leaf capacity, slot target.
+void note_canon_stats(int64_t ranges, int64_t slots_per_range, int64_t leaves, int64_t leaf_cap, int64_t target);
+void last_canon_stats(int64_t* out5);
+
 #define PAULIB_DISPATCH_WP(wp, F)                                                   \
     switch (wp) {                                                                   \
         case 1: F(1); break;                                                        \
@@ -106,7 +126,7 @@ int device_sm_count();
 // outermost active scope, so nested pipelines count toward the outer stage.
 enum Stage : int {
     ST_CONVERT = 0, ST_SAMPLE = 1, ST_COUNT = 2, ST_SCATTER = 3, ST_LEVEL2 = 4, ST_COMPACT = 5,
-    ST_RAW = 6, ST_EXPORT = 7, ST_LEAF = 8, ST_GROUP = 9
+    ST_RAW = 6, ST_EXPORT = 7, ST_LEAF = 8, ST_GROUP = 9, ST_SPLIT = 10, ST_PLACE = 11
 };
 struct StageScope {
     StageScope(int stage, cudaStream_t s);

@@ -2367,17 +2367,20 @@ static void sorted_sample(const uint64_t* samp, uint32_t S, cudaStream_t st, Scr
     check_cuda(cudaGetLastError(), "k_or_err");
 }
 
+// Level 1: every record is placed in its coarse key range.  Fills rec (the
+// records grouped by range), boff (nbk + 1 range offsets) and bflags (1 for a
+// range holding one repeated key); subid is scratch for the per-record range
+// ids.  With Reff <= C1 there is one range holding every record in order.
+// Returns nbk.  Device errors of the sample sort are or-ed into err.
+// bmax caps the number of coarse ranges (the counting kernel keeps two 8-byte
+// codes per splitter in shared memory: at most 2 * (bmax - 1) <= 4094).
 template <class Src, int MODE>
-static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStream_t st, Staged& out) {
+static uint32_t level1_partition(const Src& src, uint32_t R, uint32_t nb_terms, uint64_t C1, uint32_t bmax,
+                                 int oversample, int count_ctas_per_sm, cudaStream_t st, uint32_t* rec,
+                                 uint16_t* subid, Scratch& boff_s, Scratch& bflags_s, int32_t* err) {
     constexpr int NW = Src::NW;
     constexpr int WP = Src::WP;
-    using Cfg = L2Cfg<Src, MODE>;
-    constexpr uint32_t CAP = Cfg::CAP;
     const int sms = device_sm_count();
-
-    out.err = Scratch(4, st);
-    check_cuda(cudaMemsetAsync(out.err.p, 0, 4, st), "memset err");
-    // R indexes the record space; Reff records exist (fewer for a symmetric product)
     uint32_t sym_na = 0;
     uint64_t Reff = R;
     if constexpr (IsProd<Src>::value) {
@@ -2386,48 +2389,41 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
             Reff = (uint64_t)src.na * (src.na + 1) / 2;
         }
     }
-    Scratch recA((size_t)Reff * 4, st), recB((size_t)Reff * 4, st), subid((size_t)R * 2, st);
-    Scratch bflags_s, cnt_s, boff_s;
-    uint32_t nbk = 1;
-    const Tuning tune = tuning_for(NW);
-    const uint64_t C1 = (uint64_t)CAP * (uint64_t)tune.coarse_factor;
-
     if (Reff <= C1) {
         StageScope ss(ST_SCATTER, st);
         boff_s = Scratch(16, st);
         bflags_s = Scratch(1, st);
         if (sym_na)
-            k_iota_tri<<<(unsigned)((Reff + 255) / 256), 256, 0, st>>>(recA.as<uint32_t>(), (uint32_t)Reff, sym_na,
+            k_iota_tri<<<(unsigned)((Reff + 255) / 256), 256, 0, st>>>(rec, (uint32_t)Reff, sym_na,
                                                                      boff_s.as<uint64_t>(), bflags_s.as<uint8_t>());
         else
-            k_iota<<<(R + 255) / 256, 256, 0, st>>>(recA.as<uint32_t>(), R, boff_s.as<uint64_t>(),
-                                                    bflags_s.as<uint8_t>());
+            k_iota<<<(R + 255) / 256, 256, 0, st>>>(rec, R, boff_s.as<uint64_t>(), bflags_s.as<uint8_t>());
         note_launch(ST_SCATTER);
         check_cuda(cudaGetLastError(), "k_iota");
-    } else {
-        const uint32_t bmax = (uint32_t)(max_coarse_splitters<NW>() / 2 + 1);
-        const uint32_t B1 = (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>(bmax, (Reff + C1 - 1) / C1));
-        const uint32_t S = (uint32_t)std::min<uint64_t>(Reff, (uint64_t)B1 * (uint64_t)tune.oversample);
-        Scratch samp((size_t)S * NW * 8, st);
-        const uint32_t nsp = 2 * (B1 - 1);
-        nbk = nsp + 1;
-        Scratch spl((size_t)nsp * NW * 8, st), pref((size_t)S * 4, st);
-        bflags_s = Scratch(nbk, st);
-        {
-            StageScope ss(ST_SAMPLE, st);
-            k_sample<Src><<<(S + 255) / 256, 256, 0, st>>>(src, R, S, g_sample_seed, samp.as<uint64_t>());
-            note_launch(ST_SAMPLE);
-            check_cuda(cudaGetLastError(), "k_sample");
-            Scratch dk, dc, du;
-            sorted_sample<NW>(samp.as<uint64_t>(), S, st, dk, dc, du, out.err.as<int32_t>());
-            k_select<NW><<<1, 1024, 0, st>>>(dk.as<uint64_t>(), dc.as<double2>(), du.as<uint64_t>(), S, B1,
-                                             pref.as<uint32_t>(), spl.as<uint64_t>(), bflags_s.as<uint8_t>());
-            note_launch(ST_SAMPLE);
-            check_cuda(cudaGetLastError(), "k_select");
-        }
-        cnt_s = Scratch((size_t)nbk * 4, st);
-        check_cuda(cudaMemsetAsync(cnt_s.p, 0, (size_t)nbk * 4, st), "memset");
-        {
+        return 1;
+    }
+    const uint32_t B1 = (uint32_t)std::max<uint64_t>(2, std::min<uint64_t>(bmax, (Reff + C1 - 1) / C1));
+    const uint32_t S = (uint32_t)std::min<uint64_t>(Reff, (uint64_t)B1 * (uint64_t)oversample);
+    Scratch samp((size_t)S * NW * 8, st);
+    const uint32_t nsp = 2 * (B1 - 1);
+    const uint32_t nbk = nsp + 1;
+    Scratch spl((size_t)nsp * NW * 8, st), pref((size_t)S * 4, st);
+    bflags_s = Scratch(nbk, st);
+    {
+        StageScope ss(ST_SAMPLE, st);
+        k_sample<Src><<<(S + 255) / 256, 256, 0, st>>>(src, R, S, g_sample_seed, samp.as<uint64_t>());
+        note_launch(ST_SAMPLE);
+        check_cuda(cudaGetLastError(), "k_sample");
+        Scratch dk, dc, du;
+        sorted_sample<NW>(samp.as<uint64_t>(), S, st, dk, dc, du, err);
+        k_select<NW><<<1, 1024, 0, st>>>(dk.as<uint64_t>(), dc.as<double2>(), du.as<uint64_t>(), S, B1,
+                                         pref.as<uint32_t>(), spl.as<uint64_t>(), bflags_s.as<uint8_t>());
+        note_launch(ST_SAMPLE);
+        check_cuda(cudaGetLastError(), "k_select");
+    }
+    Scratch cnt_s((size_t)nbk * 4, st);
+    check_cuda(cudaMemsetAsync(cnt_s.p, 0, (size_t)nbk * 4, st), "memset");
+    {
         StageScope ssc(ST_COUNT, st);
         Scratch codes((size_t)nsp * 16, st), meta(16, st);
         k_spl_codes<NW><<<1, 1024, 0, st>>>(spl.as<uint64_t>(), nsp, codes.as<uint64_t>(), meta.as<uint32_t>());
@@ -2439,41 +2435,62 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
             const uint64_t tiles = (uint64_t)((src.na + kCountThreads - 1) / kCountThreads) *
                                    ((nb_terms + kCountCols - 1) / kCountCols);
             const unsigned grid = (unsigned)std::max<uint64_t>(
-                1, std::min<uint64_t>(tiles, (uint64_t)sms * (uint64_t)tune.count_ctas_per_sm));
+                1, std::min<uint64_t>(tiles, (uint64_t)sms * (uint64_t)count_ctas_per_sm));
             kern<<<grid, kCountThreads, sm, st>>>(src, nb_terms, spl.as<uint64_t>(), codes.as<uint64_t>(),
-                                                 meta.as<uint32_t>(), nsp, subid.as<uint16_t>(),
-                                                 cnt_s.as<uint32_t>());
+                                                 meta.as<uint32_t>(), nsp, subid, cnt_s.as<uint32_t>());
         } else {
             const size_t sm = count_smem<NW>(nsp, false);
             auto kern = k_count_lin<Src>;
             smem_attr(kern, sm);
             const unsigned grid = (unsigned)std::max<uint64_t>(
                 1, std::min<uint64_t>(((uint64_t)R + kCountThreads - 1) / kCountThreads,
-                                      (uint64_t)sms * (uint64_t)tune.count_ctas_per_sm));
+                                      (uint64_t)sms * (uint64_t)count_ctas_per_sm));
             kern<<<grid, kCountThreads, sm, st>>>(src, R, spl.as<uint64_t>(), codes.as<uint64_t>(),
-                                                 meta.as<uint32_t>(), nsp, subid.as<uint16_t>(),
-                                                 cnt_s.as<uint32_t>());
+                                                 meta.as<uint32_t>(), nsp, subid, cnt_s.as<uint32_t>());
         }
         note_launch(ST_COUNT);
         check_cuda(cudaGetLastError(), "k_count");
-        }
-        StageScope ssx(ST_SCATTER, st);
-        boff_s = Scratch((size_t)(nbk + 1) * 8, st);
-        k_scan_counts<<<1, 1024, 0, st>>>(cnt_s.as<uint32_t>(), nbk, boff_s.as<uint64_t>());
-        note_launch(ST_SCATTER);
-        Scratch cursor((size_t)nbk * 8, st);
-        check_cuda(cudaMemcpyAsync(cursor.p, boff_s.p, (size_t)nbk * 8, cudaMemcpyDeviceToDevice, st), "cursor");
-        const size_t sm = (size_t)((nbk + 1) & ~1u) * 4 + (size_t)((nbk + 2) & ~1u) * 4 + (size_t)nbk * 8 +
-                          (size_t)kScatterChunk * 6;
-        smem_attr(k_scatter, sm);
-        const uint64_t per_sm = std::max<uint64_t>(1, (220u * 1024u) / (sm + 1024u));
-        const unsigned grid = (unsigned)std::max<uint64_t>(
-            1, std::min<uint64_t>(((uint64_t)R + kScatterChunk - 1) / kScatterChunk, (uint64_t)sms * per_sm));
-        k_scatter<<<grid, kScatterThreads, sm, st>>>(subid.as<uint16_t>(), R, nbk, cursor.as<uint64_t>(),
-                                                    recA.as<uint32_t>(), sym_na);
-        note_launch(ST_SCATTER);
-        check_cuda(cudaGetLastError(), "k_scatter");
     }
+    StageScope ssx(ST_SCATTER, st);
+    boff_s = Scratch((size_t)(nbk + 1) * 8, st);
+    k_scan_counts<<<1, 1024, 0, st>>>(cnt_s.as<uint32_t>(), nbk, boff_s.as<uint64_t>());
+    note_launch(ST_SCATTER);
+    Scratch cursor((size_t)nbk * 8, st);
+    check_cuda(cudaMemcpyAsync(cursor.p, boff_s.p, (size_t)nbk * 8, cudaMemcpyDeviceToDevice, st), "cursor");
+    const size_t sm = (size_t)((nbk + 1) & ~1u) * 4 + (size_t)((nbk + 2) & ~1u) * 4 + (size_t)nbk * 8 +
+                      (size_t)kScatterChunk * 6;
+    smem_attr(k_scatter, sm);
+    const uint64_t per_sm = std::max<uint64_t>(1, (220u * 1024u) / (sm + 1024u));
+    const unsigned grid = (unsigned)std::max<uint64_t>(
+        1, std::min<uint64_t>(((uint64_t)R + kScatterChunk - 1) / kScatterChunk, (uint64_t)sms * per_sm));
+    k_scatter<<<grid, kScatterThreads, sm, st>>>(subid, R, nbk, cursor.as<uint64_t>(), rec, sym_na);
+    note_launch(ST_SCATTER);
+    check_cuda(cudaGetLastError(), "k_scatter");
+    return nbk;
+}
+
+template <class Src, int MODE>
+static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStream_t st, Staged& out) {
+    constexpr int NW = Src::NW;
+    using Cfg = L2Cfg<Src, MODE>;
+    constexpr uint32_t CAP = Cfg::CAP;
+    const int sms = device_sm_count();
+
+    out.err = Scratch(4, st);
+    check_cuda(cudaMemsetAsync(out.err.p, 0, 4, st), "memset err");
+    // R indexes the record space; Reff records exist (fewer for a symmetric product)
+    uint64_t Reff = R;
+    if constexpr (IsProd<Src>::value) {
+        if (src.sym) Reff = (uint64_t)src.na * (src.na + 1) / 2;
+    }
+    Scratch recA((size_t)Reff * 4, st), recB((size_t)Reff * 4, st), subid((size_t)R * 2, st);
+    Scratch bflags_s, boff_s;
+    const Tuning tune = tuning_for(NW);
+    const uint64_t C1 = (uint64_t)CAP * (uint64_t)tune.coarse_factor;
+    const uint32_t nbk = level1_partition<Src, MODE>(src, R, nb_terms, C1,
+                                                     (uint32_t)(max_coarse_splitters<NW>() / 2 + 1), tune.oversample,
+                                                     tune.count_ctas_per_sm, st, recA.as<uint32_t>(),
+                                                     subid.as<uint16_t>(), boff_s, bflags_s, out.err.as<int32_t>());
 
     // level 2 and the leaves
     constexpr uint32_t WL = warp_leaf_cap<NW>();
@@ -2533,55 +2550,6 @@ static paulib_sum* empty_canonical(int32_t n_qubits, cudaStream_t st) {
     paulib_sum* out = sum_alloc(n_qubits, 0, false, st);
     out->is_canonical = 1;
     return out;
-}
-
-template <int WP, int MODE>
-static paulib_sum* product_mode(const paulib_sum* a, const paulib_sum* b, cudaStream_t st) {
-    using Src = ProdSrc<WP, MODE>;
-    using V = typename Src::V;
-    const uint32_t R = (uint32_t)(a->n_terms * b->n_terms);
-    Scratch fa, fb;
-    const V* ac;
-    const V* bc;
-    if constexpr (MODE == M_FP64) {
-        ac = reinterpret_cast<const V*>(a->coef);
-        bc = reinterpret_cast<const V*>(b->coef);
-    } else {
-        fa = Scratch((size_t)a->n_terms * 8, st);
-        fb = Scratch((size_t)b->n_terms * 8, st);
-        StageScope ss(ST_CONVERT, st);
-        k_to_f32<MODE><<<(unsigned)((a->n_terms + 255) / 256), 256, 0, st>>>(a->coef, fa.as<float2>(), a->n_terms);
-        k_to_f32<MODE><<<(unsigned)((b->n_terms + 255) / 256), 256, 0, st>>>(b->coef, fb.as<float2>(), b->n_terms);
-        note_launch(ST_CONVERT);
-        note_launch(ST_CONVERT);
-        check_cuda(cudaGetLastError(), "k_to_f32");
-        ac = fa.as<V>();
-        bc = fb.as<V>();
-    }
-    // the same sum on both sides: only i <= j pairs are generated
-    Src src{a->keys, b->keys, a->pbase, b->pbase, ac, bc, (uint32_t)a->n_terms, a == b ? 1u : 0u,
-            recip64((uint32_t)a->n_terms)};
-    return finish<Src, MODE>(src, R, (uint32_t)b->n_terms, a->n_qubits, st);
-}
-
-template <int WP, int MODE>
-static paulib_sum* terms_mode(const paulib_sum* in, cudaStream_t st) {
-    using Src = TermSrc<WP, MODE>;
-    using V = typename Src::V;
-    Scratch f;
-    const V* c;
-    if constexpr (MODE == M_FP64) {
-        c = reinterpret_cast<const V*>(in->coef);
-    } else {
-        f = Scratch((size_t)in->n_terms * 8, st);
-        StageScope ss(ST_CONVERT, st);
-        k_to_f32<MODE><<<(unsigned)((in->n_terms + 255) / 256), 256, 0, st>>>(in->coef, f.as<float2>(), in->n_terms);
-        note_launch(ST_CONVERT);
-        check_cuda(cudaGetLastError(), "k_to_f32");
-        c = f.as<V>();
-    }
-    Src src{in->keys, in->phase, c};
-    return finish<Src, MODE>(src, (uint32_t)in->n_terms, 0, in->n_qubits, st);
 }
 
 }  // namespace paulib

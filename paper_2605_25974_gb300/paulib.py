@@ -28,9 +28,11 @@ EXPORTED = ["paulib_abi_version", "paulib_sum_create", "paulib_sum_info", "pauli
             "paulib_multiply_noalloc", "paulib_batch_plan_create", "paulib_batch_plan_launch",
             "paulib_batch_plan_outputs", "paulib_batch_plan_destroy", "paulib_set_tuning",
             "paulib_apply_clifford", "paulib_rotate", "paulib_multiply_pairwise",
-            "paulib_group_commuting", "paulib_set_group_candidates"]
+            "paulib_group_commuting", "paulib_set_group_candidates", "paulib_set_slot_tuning",
+            "paulib_last_canon_method", "paulib_sum_export_range", "paulib_last_canon_stats"]
 GATES = {"h": 0, "s": 1, "cnot": 2, "cz": 3}
-STAGES = ["convert", "sample", "count", "scatter", "level2", "compact", "raw", "export", "leaf", "group"]
+STAGES = ["convert", "sample", "count", "scatter", "level2", "compact", "raw", "export", "leaf", "group", "split",
+          "place"]
 
 
 class PaulibError(RuntimeError):
@@ -95,6 +97,14 @@ def load(path: Optional[str] = None):
     lib.paulib_group_commuting.restype = _i32
     lib.paulib_set_group_candidates.argtypes = [_i32]
     lib.paulib_set_group_candidates.restype = _i32
+    lib.paulib_set_slot_tuning.argtypes = [_i32, _i32, _i32, _i32, _i32]
+    lib.paulib_set_slot_tuning.restype = _i32
+    lib.paulib_last_canon_method.argtypes = [ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
+    lib.paulib_last_canon_method.restype = _i32
+    lib.paulib_sum_export_range.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp]
+    lib.paulib_sum_export_range.restype = _i32
+    lib.paulib_last_canon_stats.argtypes = [ctypes.POINTER(_i64)]
+    lib.paulib_last_canon_stats.restype = _i32
     for name in ("paulib_sum_create", "paulib_sum_info", "paulib_sum_export", "paulib_multiply",
                  "paulib_compress", "paulib_multiply_batched", "paulib_set_allocator"):
         getattr(lib, name).restype = _i32
@@ -192,6 +202,25 @@ class PauliSum:
                 torch.cuda.synchronize()
         return x, z, c, k
 
+    def export_range(self, first, count, stream=None, with_phase=False):
+        """Copies terms [first, first + count) out into new host arrays."""
+        W = self.words
+        x = np.zeros((W, count), np.uint64)
+        z = np.zeros((W, count), np.uint64)
+        c = np.zeros(count, np.complex128)
+        k = np.zeros(count, np.uint8) if with_phase else None
+        st = _stream(stream)
+        _check(load().paulib_sum_export_range(_vp(self._h), ctypes.c_int64(first), ctypes.c_int64(count), _ptr(x),
+                                              _ptr(z), _ptr(c), _ptr(k), _vp(st)))
+        import torch
+        if stream is None:
+            torch.cuda.current_stream().synchronize()
+        elif hasattr(stream, "synchronize"):
+            stream.synchronize()
+        else:
+            torch.cuda.synchronize()
+        return x, z, c, k
+
     def close(self):
         if self._h:
             load().paulib_sum_destroy(_vp(self._h))
@@ -264,6 +293,25 @@ class BatchPlan:
         _check(load().paulib_batch_plan_outputs(_vp(self._h), _vp(_stream(stream)), O))
         return [_Borrowed(O[i]) for i in range(self.batch)]
 
+    def export_range(self, first, count, stream=None, with_phase=False):
+        """Copies terms [first, first + count) out into new host arrays."""
+        W = self.words
+        x = np.zeros((W, count), np.uint64)
+        z = np.zeros((W, count), np.uint64)
+        c = np.zeros(count, np.complex128)
+        k = np.zeros(count, np.uint8) if with_phase else None
+        st = _stream(stream)
+        _check(load().paulib_sum_export_range(_vp(self._h), ctypes.c_int64(first), ctypes.c_int64(count), _ptr(x),
+                                              _ptr(z), _ptr(c), _ptr(k), _vp(st)))
+        import torch
+        if stream is None:
+            torch.cuda.current_stream().synchronize()
+        elif hasattr(stream, "synchronize"):
+            stream.synchronize()
+        else:
+            torch.cuda.synchronize()
+        return x, z, c, k
+
     def close(self):
         if self._h:
             load().paulib_batch_plan_destroy(_vp(self._h))
@@ -293,6 +341,31 @@ def set_tuning(key_words=0, coarse_factor=0, oversample=0, count_ctas_per_sm=0, 
     """Pipeline tuning for keys of ``key_words`` words (0 = all); 0 keeps a value."""
     _check(load().paulib_set_tuning(int(key_words), int(coarse_factor), int(oversample), int(count_ctas_per_sm),
                                     int(range_ctas_per_sm)))
+
+
+def set_slot_tuning(key_words=0, method=-1, leaf_cap=-1, slot_target=-1, slot_oversample=-1):
+    """Canonicalisation method (0 slot sort, 1 range sort) and slot-sort
+    tuning for keys of ``key_words`` words (0 = all): -1 keeps a value, 0
+    restores its default."""
+    _check(load().paulib_set_slot_tuning(int(key_words), int(method), int(leaf_cap), int(slot_target),
+                                         int(slot_oversample)))
+
+
+def last_canon_method():
+    """(method, fallback_bits) of this thread's last canonical result: method 0
+    slot sort, 1 range sort; fallback_bits nonzero when the slot sort handed
+    the call to the range sort."""
+    m, b = _i32(), _i32()
+    _check(load().paulib_last_canon_method(ctypes.byref(m), ctypes.byref(b)))
+    return int(m.value), int(b.value)
+
+
+def last_canon_stats():
+    """Shape of this thread's last slot sort: ranges, slot capacity per range,
+    leaves, leaf capacity, slot target."""
+    v = (_i64 * 5)()
+    _check(load().paulib_last_canon_stats(v))
+    return dict(zip(("ranges", "slots_per_range", "leaves", "leaf_cap", "slot_target"), [int(q) for q in v]))
 
 
 def apply_clifford(s: "PauliSum", gates, stream=None):
