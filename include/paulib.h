@@ -214,7 +214,7 @@ paulib_status paulib_multiply_noalloc(int32_t n_qubits, int64_t na, const uint64
  * words (2*WP for products and compress, 2*WP + 2 for batched products; 0 =
  * every size).  No counterpart in the paper; results never depend on it.
  *   coarse_factor: a first-level key range targets coarse_factor x the
- *       shared-memory leaf capacity records (2..256, default 16);
+ *       shared-memory leaf capacity records (2..256, default 32);
  *   oversample: splitter sample size per first-level range (4..128, default 32);
  *   count_ctas_per_sm: CTAs per SM of the first-level counting kernel (1..16);
  *   range_ctas_per_sm: CTAs per SM of the range sort/merge kernel (1..2).
@@ -257,7 +257,18 @@ paulib_status paulib_set_slot_tuning(int32_t key_words, int32_t method, int32_t 
  * Errors: INVALID_ARG for NULL pointers.                                    */
 paulib_status paulib_last_canon_method(int32_t* method, int32_t* fallback_bits);
 
-/* Shape of the calling thread's last slot sort, for tuning: stats[0] coarse
+/* Test settings (no counterpart in the paper; 0 turns a setting off, the
+ * default).  Results never depend on them except as stated.
+ *   knob 1, value 1..63: the range sort's warp leaves keep only the low
+ *     `value` bits of their 64-bit key hashes, so different keys of a leaf
+ *     share hashes and the leaf takes its whole-key path (the same result).
+ *   knob 2, value 1..4096: a range CTA's worklist holds `value` entries; a
+ *     split that needs more sets the device error word and returns, and the
+ *     call fails with PAULIB_ERR_INTERNAL (no result).
+ * Errors: INVALID_ARG for an unknown knob or a value out of range.          */
+paulib_status paulib_set_debug(int32_t knob, int64_t value);
+
+/* Shape of the calling thread's last slot sort, for tuning/* Shape of the calling thread's last slot sort, for tuning: stats[0] coarse
  * ranges, [1] slot capacity per range, [2] leaves, [3] terms per leaf (the
  * capacity), [4] mean terms per slot aimed at.  All zero before the first
  * slot sort.  No counterpart in the paper.  Errors: INVALID_ARG (NULL).      */

@@ -374,6 +374,22 @@ void set_slot_tuning(int key_words, const SlotTuning& t, bool) {
     g_slot_by_words.push_back({key_words, t});
 }
 
+namespace {
+std::mutex g_debug_mu;
+DebugSettings g_debug;
+}  // namespace
+
+DebugSettings debug_settings() {
+    std::lock_guard<std::mutex> lk(g_debug_mu);
+    return g_debug;
+}
+
+void set_debug(int knob, int64_t value) {
+    std::lock_guard<std::mutex> lk(g_debug_mu);
+    if (knob == 1) g_debug.hash_bits = (int)value;
+    else if (knob == 2) g_debug.stack_cap = (int)value;
+}
+
 void note_canon_method(int method, int bits) {
     g_canon_method = method;
     g_canon_bits = bits;
@@ -863,6 +879,20 @@ paulib_status paulib_set_slot_tuning(int32_t key_words, int32_t method, int32_t 
     if (slot_target >= 0) t.target = slot_target;
     if (slot_oversample >= 0) t.oversample = slot_oversample;
     set_slot_tuning(key_words, t, true);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_set_debug(int32_t knob, int64_t value) {
+    PAULIB_API_BEGIN
+    if (knob == 1) {
+        if (value < 0 || value > 64) fail(PAULIB_ERR_INVALID_ARG, "hash bits must be 0..64");
+    } else if (knob == 2) {
+        if (value < 0 || value > 4096) fail(PAULIB_ERR_INVALID_ARG, "stack capacity must be 0..4096");
+    } else {
+        fail(PAULIB_ERR_INVALID_ARG, "unknown debug setting " + std::to_string(knob));
+    }
+    set_debug(knob, value);
     return PAULIB_OK;
     PAULIB_API_END
 }

@@ -91,6 +91,17 @@ struct Tuning {
 Tuning tuning_for(int key_words);
 void set_tuning(int key_words, const Tuning& t);
 
+// Test settings (paulib_set_debug); 0 = off.  hash_bits: keep only the low
+// hash_bits bits of the range sort's warp-leaf key hashes (forces the
+// hash-clash path); stack_cap: entries of a range CTA's worklist (a small cap
+// makes the split raise its stack error and return).
+struct DebugSettings {
+    int hash_bits = 0;
+    int stack_cap = 0;
+};
+DebugSettings debug_settings();
+void set_debug(int knob, int64_t value);
+
 // Canonicalisation method and slot-sort tuning (paulib_set_slot_tuning);
 // never changes results.  0 fields mean the built-in default.
 struct SlotTuning {

@@ -1211,7 +1211,19 @@ struct L2Bufs {
     uint2* med;    // leaves for one CTA
     uint32_t small_cap, med_cap;
     int32_t* err;
+    // Test settings (paulib_set_debug): the warp leaves' key hashes are
+    // and-ed with hash_mask (narrow masks force the hash-clash path), and a
+    // range CTA's worklist holds stack_cap entries (at most kStackCap).
+    uint64_t hash_mask = ~0ull;
+    uint32_t stack_cap = (uint32_t)kStackCap;
 };
+
+// Applies the test settings of paulib_set_debug to a launch's buffers.
+inline void apply_debug(L2Bufs& b) {
+    const DebugSettings d = debug_settings();
+    if (d.hash_bits > 0 && d.hash_bits < 64) b.hash_mask = (1ull << d.hash_bits) - 1ull;
+    if (d.stack_cap > 0 && d.stack_cap < kStackCap) b.stack_cap = (uint32_t)d.stack_cap;
+}
 
 // ---- block leaf: one CTA orders a range of at most CAP records in shared
 // memory and sums each run of equal keys with a block segmented scan.
@@ -1681,7 +1693,7 @@ __device__ __forceinline__ uint64_t key_hash(const uint64_t (&k)[NW]) {
 // the whole key.
 template <class Src, int MODE, int NW, uint32_t WL, uint32_t EPL>
 __device__ void warp_leaf_rows(const Src& src, const uint32_t* cur, uint32_t lo, uint32_t n, unsigned char* wsm,
-                               uint64_t* Tkeys, double2* Tcoef, uint8_t* oflag) {
+                               uint64_t* Tkeys, double2* Tcoef, uint8_t* oflag, uint64_t hmask) {
     static_assert(EPL * 32 <= WL && WL <= 128, "network fits the slice");
     using V = typename Src::V;
     uint64_t* wk = reinterpret_cast<uint64_t*>(wsm);                   // [NW][WL]
@@ -1702,7 +1714,7 @@ __device__ void warp_leaf_rows(const Src& src, const uint32_t* cur, uint32_t lo,
             wr[t] = r;
             vr[e] = src.value(r, k);
             skey_store<NW>(wk, WL, t, k);
-            hh[e] = key_hash<NW>(k);
+            hh[e] = key_hash<NW>(k) & hmask;
         } else {
             wr[t] = 0xffffffffu;
         }
@@ -1773,17 +1785,19 @@ __device__ void warp_leaf_rows(const Src& src, const uint32_t* cur, uint32_t lo,
 // A warp leaf sorts with the smallest network that holds its n records.
 template <class Src, int MODE, int NW, uint32_t WL>
 __device__ __forceinline__ void warp_leaf(const Src& src, const uint32_t* cur, uint32_t lo, uint32_t n,
-                                          unsigned char* wsm, uint64_t* Tkeys, double2* Tcoef, uint8_t* oflag) {
+                                          unsigned char* wsm, uint64_t* Tkeys, double2* Tcoef, uint8_t* oflag,
+                                          uint64_t hmask) {
     if (n <= 32) {
-        warp_leaf_rows<Src, MODE, NW, WL, 1>(src, cur, lo, n, wsm, Tkeys, Tcoef, oflag);
+        warp_leaf_rows<Src, MODE, NW, WL, 1>(src, cur, lo, n, wsm, Tkeys, Tcoef, oflag, hmask);
         return;
     }
     if constexpr (WL >= 64) {
         if (n <= 64) {
-            warp_leaf_rows<Src, MODE, NW, WL, 2>(src, cur, lo, n, wsm, Tkeys, Tcoef, oflag);
+            warp_leaf_rows<Src, MODE, NW, WL, 2>(src, cur, lo, n, wsm, Tkeys, Tcoef, oflag, hmask);
             return;
         }
-        if constexpr (WL >= 128) warp_leaf_rows<Src, MODE, NW, WL, 4>(src, cur, lo, n, wsm, Tkeys, Tcoef, oflag);
+        if constexpr (WL >= 128)
+            warp_leaf_rows<Src, MODE, NW, WL, 4>(src, cur, lo, n, wsm, Tkeys, Tcoef, oflag, hmask);
     }
 }
 
@@ -1855,7 +1869,7 @@ __global__ void __launch_bounds__(kWarpLeafWarps * 32) k_leaf_warp(Src src, L2Bu
         const uint32_t* cur = (en.y >> 31) ? b.recB : b.recA;
         const uint32_t n = en.y & 0x3fffffffu;
         if (en.y & 0x40000000u) warp_uniform<Src, MODE>(src, cur, en.x, n, b.Tkeys, b.Tcoef, b.oflag);
-        else warp_leaf<Src, MODE, NW, WL>(src, cur, en.x, n, wsm, b.Tkeys, b.Tcoef, b.oflag);
+        else warp_leaf<Src, MODE, NW, WL>(src, cur, en.x, n, wsm, b.Tkeys, b.Tcoef, b.oflag, b.hash_mask);
     }
 }
 
@@ -1905,7 +1919,7 @@ __device__ __forceinline__ void route_range(const Src& src, const L2Bufs& b, boo
     }
     if (kind == 3) {
         const uint32_t p = atomicAdd(s_sp, 1u);
-        if (p < (uint32_t)kStackCap) stack[p] = StackEnt{lo, lo + n, fl, 0u};
+        if (p < b.stack_cap) stack[p] = StackEnt{lo, lo + n, fl, 0u};
         else atomicOr(b.err, ERR_STACK);
     }
 }
@@ -1954,7 +1968,7 @@ __global__ void __launch_bounds__(kL2Threads, 2) k_level2(Src src, uint32_t nbk,
         uint32_t iters = 0;
         for (;;) {
             if (tid == 0) {
-                if (s_sp == 0 || s_bad || s_sp > (uint32_t)kStackCap) {
+                if (s_sp == 0 || s_bad || s_sp > b.stack_cap) {
                     s_done = 1;
                 } else {
                     const StackEnt e = stack[--s_sp];
@@ -2513,6 +2527,7 @@ static void run_pipeline(const Src& src, uint32_t R, uint32_t nb_terms, cudaStre
              stacks.as<StackEnt>(), splscr.as<uint64_t>(), out.Tkeys.as<uint64_t>(), out.Tcoef.as<double2>(),
              out.oflag.as<uint8_t>(), lists.as<uint2>(), lists.as<uint2>() + small_cap, small_cap, med_cap,
              out.err.as<int32_t>()};
+    apply_debug(b);
     launch_level2<Src, MODE>(src, nbk, boff_s.as<uint64_t>(), bflags_s.as<uint8_t>(), b, grid2, out.nch,
                              ccount.as<uint32_t>(), out.coff.as<uint64_t>(), st);
 }

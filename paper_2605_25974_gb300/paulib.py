@@ -29,7 +29,7 @@ EXPORTED = ["paulib_abi_version", "paulib_sum_create", "paulib_sum_info", "pauli
             "paulib_batch_plan_outputs", "paulib_batch_plan_destroy", "paulib_set_tuning",
             "paulib_apply_clifford", "paulib_rotate", "paulib_multiply_pairwise",
             "paulib_group_commuting", "paulib_set_group_candidates", "paulib_set_slot_tuning",
-            "paulib_last_canon_method", "paulib_sum_export_range", "paulib_last_canon_stats"]
+            "paulib_last_canon_method", "paulib_sum_export_range", "paulib_last_canon_stats", "paulib_set_debug"]
 GATES = {"h": 0, "s": 1, "cnot": 2, "cz": 3}
 STAGES = ["convert", "sample", "count", "scatter", "level2", "compact", "raw", "export", "leaf", "group", "split",
           "place"]
@@ -105,6 +105,8 @@ def load(path: Optional[str] = None):
     lib.paulib_sum_export_range.restype = _i32
     lib.paulib_last_canon_stats.argtypes = [ctypes.POINTER(_i64)]
     lib.paulib_last_canon_stats.restype = _i32
+    lib.paulib_set_debug.argtypes = [_i32, _i64]
+    lib.paulib_set_debug.restype = _i32
     for name in ("paulib_sum_create", "paulib_sum_info", "paulib_sum_export", "paulib_multiply",
                  "paulib_compress", "paulib_multiply_batched", "paulib_set_allocator"):
         getattr(lib, name).restype = _i32
@@ -358,6 +360,13 @@ def last_canon_method():
     m, b = _i32(), _i32()
     _check(load().paulib_last_canon_method(ctypes.byref(m), ctypes.byref(b)))
     return int(m.value), int(b.value)
+
+
+def set_debug(knob, value):
+    """Test settings: knob 1 = warp-leaf hash bits kept (forces the hash-clash
+    path), knob 2 = range-CTA worklist capacity (forces the stack error);
+    value 0 turns a setting off."""
+    _check(load().paulib_set_debug(int(knob), int(value)))
 
 
 def last_canon_stats():

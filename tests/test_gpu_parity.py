@@ -368,3 +368,29 @@ def test_export_pinned_even_and_odd_counts(lib, m):
     assert np.array_equal(px.numpy().view(np.uint64), nx) and np.array_equal(pz.numpy().view(np.uint64), nz)
     assert np.array_equal(nx, s.x) and np.array_equal(nz, s.z) and np.array_equal(nc, s.c)
     assert np.array_equal(pc.numpy()[:, 0], s.c.real) and np.array_equal(pc.numpy()[:, 1], s.c.imag)
+
+
+@pytest.mark.parametrize("n,ma,mb,phases", [(100, 300, 37, False), (200, 129, 33, True), (500, 257, 31, False),
+                                            (1024, 131, 45, True), (128, 127, 32, False), (65, 1, 1, True),
+                                            (256, 130, 1, False)])
+def test_raw_outer_product_every_word_width(lib, oracle, n, ma, mb, phases):
+    # The tiled raw kernel (128 left terms per CTA x 32 right terms, keys
+    # staged per warp) at 2, 4, 8 and 16 padded words per half, with ragged
+    # last tiles in both directions (|A| not a multiple of 128, |B| not of
+    # 32) and operand phases: keys and phases bit-exact, c_a*c_b within the
+    # one-FMA bound, against the oracle's qubit-by-qubit products.
+    from paper_2605_25974_gb300 import workloads as wl
+    rng = wl.rng_for(5 * n + ma)
+    ax, az = wl.weighted_random(rng, n, ma, 1, min(n, 40))
+    bx, bz = wl.weighted_random(rng, n, mb, 1, min(n, 40))
+    ka = rng.integers(0, 4, ma).astype(np.uint8) if phases else None
+    kb = rng.integers(0, 4, mb).astype(np.uint8) if phases else None
+    a = wl.SumArrays(n, ax, az, wl.coeffs_normal(rng, ma), ka)
+    b = wl.SumArrays(n, bx, bz, wl.coeffs_normal(rng, mb), kb)
+    with gpu_sum(lib, a) as ga, gpu_sum(lib, b) as gb, lib.multiply(ga, gb, canonical=False) as gr:
+        assert gr.n_terms == ma * mb and not gr.is_canonical
+        x, z, c, k = gr.export()
+    ox, oz, oc, ok = oracle.multiply_raw(n, a.as_tuple(), b.as_tuple())
+    assert np.array_equal(x, ox) and np.array_equal(z, oz) and np.array_equal(k, ok)
+    bound = 4 * 2.0 ** -53 * np.abs(np.repeat(b.c, ma)) * np.abs(np.tile(a.c, mb))
+    assert np.all(np.abs(c.real - oc.real) <= bound) and np.all(np.abs(c.imag - oc.imag) <= bound)
