@@ -27,17 +27,8 @@ if ROOT not in sys.path:
 METRIC = "merged Pauli products/s (H·H), mixed vs FP64 at equal error; % of roofline"
 UNIT = "products/s"
 HBM_PEAK_FALLBACK = 6800.0
-# FP64 peak derived from unit counts: 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
-FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
-
-# DRAM bytes (read + write) per product of a stage's kernels in one timed
-# step, from ncu counters (dram__bytes_read.sum + dram__bytes_write.sum) on
-# the 30,000-term n=200 workload (summarised under profiles/); keyed by
-# (stage, n_qubits).  Entries must be removed when those kernels change.
-TRAFFIC_PER_PRODUCT = {
-    ("leaf", 200): 42.80e9 / 9e8,    # k_leaf_warp + k_leaf_block
-    ("level2", 200): 24.27e9 / 9e8,  # k_level2
-}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+PIPELINE_SRC = os.path.join(ROOT, "paper_2605_25974_gb300", "csrc", "paulib_pipeline.cuh")
 
 WORKLOADS = {
     "jw_hh_n200_m30000": dict(n=200, m=30000, seed=401),
@@ -143,26 +134,69 @@ def make_workload(name):
 
 # ------------------------------------------------------------------ CPU oracle leg
 
-def oracle_rate(h, budget_s=10.0):
-    """The oracle as it stands, single-threaded, on a bounded sample: the
-    canonical product of the first m' terms of H with themselves."""
+def cpu_info():
+    """Host CPU model and logical core count."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"model": model or "unknown", "nproc": os.cpu_count() or 1}
+
+
+def oracle_rate(h, budget_s=10.0, threads=1):
+    """The oracle as it stands on a bounded sample: the canonical product of
+    the first m' terms of H with themselves, m' chosen so one run takes about
+    budget_s.  threads=1 runs the plain ordered-map mode; more threads run
+    the oracle's multi-threaded sort-and-merge mode over the whole key
+    range."""
     from oracle import pauli_oracle
     pauli_oracle._load()
 
     def run(mp):
         s = h.subset(slice(0, mp))
         t0 = time.perf_counter()
-        pauli_oracle.multiply_canonical(h.n, s.as_tuple(), s.as_tuple())
+        if threads == 1:
+            pauli_oracle.multiply_canonical(h.n, s.as_tuple(), s.as_tuple())
+        else:
+            pauli_oracle.multiply_canonical_range(h.n, s.as_tuple(), s.as_tuple(), None, None, threads)
         return time.perf_counter() - t0
 
-    probe = 200
+    probe = 300 if threads == 1 else 1200
     t = run(probe)
     rate = probe * probe / max(t, 1e-6)
     mp = int(min(h.m, max(probe, (rate * budget_s) ** 0.5)))
     t = run(mp)
-    return {"value": mp * mp / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "canonical product of the first %d terms of H with themselves (%d products, %.1f s)"
-                      % (mp, mp * mp, t)}, mp
+    mode = "ordered-map mode" if threads == 1 else "multi-threaded sort-and-merge mode"
+    return {"value": mp * mp / t, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "canonical product of the first %d terms of H with themselves (%d products, %.1f s, %s)"
+                      % (mp, mp * mp, t, mode)}, mp
+
+
+def oracle_baselines(h, budget_s=10.0):
+    """Single-core and all-core oracle rates with the host's CPU model."""
+    info = cpu_info()
+    one, _ = oracle_rate(h, budget_s, 1)
+    allc, _ = oracle_rate(h, budget_s, info["nproc"])
+    out = dict(allc)
+    out["cpu"] = info["model"]
+    out["nproc"] = info["nproc"]
+    out["single_core"] = one
+    return out
 
 
 def run_reference(args):
@@ -171,18 +205,21 @@ def run_reference(args):
         return
     h = make_workload(args.workload)
     from oracle import pauli_oracle
-    base, mp = oracle_rate(h, budget_s=min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    info = cpu_info()
+    threads = info["nproc"]
+    base, mp = oracle_rate(h, budget_s=min(8.0, 150.0 / max(1, args.steps + args.warmup)), threads=threads)
     s = h.subset(slice(0, mp))
     times = []
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        pauli_oracle.multiply_canonical(h.n, s.as_tuple(), s.as_tuple())
+        pauli_oracle.multiply_canonical_range(h.n, s.as_tuple(), s.as_tuple(), None, None, threads)
         dt = time.perf_counter() - t0
         if it >= args.warmup:
             times.append(dt)
     ms = 1e3 * statistics.mean(times)
     value = mp * mp / (ms / 1e3)
     base["value"] = value
+    base["cpu"] = info["model"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -190,6 +227,24 @@ def run_reference(args):
             "cpu_baseline": base,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def traffic_per_product(stage, n):
+    """DRAM bytes per product of a stage's kernels from the committed ncu
+    summary, or None when the summary is missing, is for another size, or was
+    taken on another version of the pipeline source (hash mismatch)."""
+    import hashlib
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+        with open(PIPELINE_SRC, "rb") as f:
+            src_hash = hashlib.sha256(f.read()).hexdigest()[:16]
+    except (OSError, ValueError):
+        return None, None
+    e = d.get("stages", {}).get("%s_n%d" % (stage, n))
+    if not e or d.get("pipeline_sha256_16") != src_hash:
+        return None, d.get("pipeline_sha256_16")
+    return float(e["bytes_per_product"]), src_hash
 
 
 # ------------------------------------------------------------------ GPU leg
@@ -420,6 +475,105 @@ def measure_batched(paulib, stream, flush, reps, problems=4096):
     return res
 
 
+def measure_tiny(paulib, stream, reps=200):
+    """64 x 64 terms at n=20 (every qubit uniform over I, X, Y, Z): one
+    canonical product is launch-latency bound; device time from CUDA events
+    and host time per call (the call synchronises once)."""
+    import torch
+    from paper_2605_25974_gb300 import workloads as wl
+    a, b = wl.tiny()
+    ga, gb = paulib.PauliSum.from_arrays(a), paulib.PauliSum.from_arrays(b)
+    for _ in range(10):
+        paulib.multiply(ga, gb).close()
+    torch.cuda.synchronize()
+    ev, wall = [], []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        o = paulib.multiply(ga, gb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall.append((time.perf_counter() - t0) * 1e6)
+        ev.append(e0.elapsed_time(e1) * 1e3)
+        u = o.n_terms
+        o.close()
+    ga.close()
+    gb.close()
+    us = statistics.median(ev)
+    return {"workload": "tiny_n20_64x64", "products": a.m * b.m, "distinct_out": int(u), "us_per_call": us,
+            "us_per_call_host": statistics.median(wall), "value": a.m * b.m / (us * 1e-6), "unit": UNIT}
+
+
+def measure_streaming(paulib, stream, hbm_peak, strings=256, reps=2):
+    """A 1,000,000-term sum at n=500 times 256 single strings of coefficient 1,
+    one canonical output per string (each a permutation of the sum's terms,
+    re-sorted).  Compulsory traffic: the input once, every output term
+    written once."""
+    import torch
+    from paper_2605_25974_gb300 import workloads as wl
+    t0 = time.perf_counter()
+    A, singles = wl.stream(m=1_000_000, strings=strings)
+    gen_s = time.perf_counter() - t0
+    ga = paulib.PauliSum.from_arrays(A)
+    gs = [paulib.PauliSum.from_arrays(s) for s in singles]
+    paulib.multiply(ga, gs[0]).close()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for g in gs:
+            paulib.multiply(ga, g).close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    products = A.m * strings
+    WP = 8
+    term = 16 * WP + 16 + 1
+    bound_ms = 1e3 * (A.m * term + products * term) / (hbm_peak * 1e9)
+    for g in gs:
+        g.close()
+    ga.close()
+    return {"workload": "stream_n500_1m_x256", "products": products, "ms_per_pass": ms,
+            "value": products / (ms / 1e3), "unit": UNIT, "hbm_bound_ms": bound_ms,
+            "frac_of_hbm_bound": bound_ms / ms, "generation_s": gen_s,
+            "note": "256 canonical products, one call per string, back to back on one stream"}
+
+
+def measure_hh(paulib, name, stream, flush, steps, warmup):
+    """Canonical H*H over all ordered pairs (two handles) for one workload:
+    device time per step and the library's per-stage times."""
+    import torch
+    h = make_workload(name)
+    g1, g2 = paulib.PauliSum.from_arrays(h), paulib.PauliSum.from_arrays(h)
+    for _ in range(warmup):
+        paulib.multiply(g1, g2).close()
+    torch.cuda.synchronize()
+    paulib.timing_read(reset=True)
+    paulib.timing_enable(True)
+    ts = []
+    for k in range(steps):
+        flush.fill_(k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        o = paulib.multiply(g1, g2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        u = o.n_terms
+        o.close()
+    paulib.timing_enable(False)
+    stage_ms, _ = paulib.timing_read(reset=True)
+    g1.close()
+    g2.close()
+    ms = statistics.mean(ts)
+    return {"workload": name, "products": h.m * h.m, "distinct_out": int(u), "ms_per_step": ms,
+            "value": h.m * h.m / (ms / 1e3), "unit": UNIT,
+            "stage_ms_per_step": {k: v / steps for k, v in stage_ms.items() if v}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -432,27 +586,46 @@ def run_ours(args):
     paulib.load()
     if args.coarse_factor > 0:
         paulib.set_tuning(0, args.coarse_factor, 0, 0, 0)
+    if args.method >= 0:
+        paulib.set_slot_tuning(0, args.method)
     gsizes = tuple(int(v) for v in args.grouping_sizes.split(","))
+    stream = torch.cuda.current_stream()
+    hbm_peak, peak_src = measured_peaks()
+    if args.peaks:
+        if rank == 0:
+            print(json.dumps({"pipe_peaks": paulib.measure_peaks(stream)}), flush=True)
+        return
+    if args.kernels_case:
+        # small case for kernel profiles: a raw and a canonical H*H of the
+        # 6,000-term n=200 Jordan-Wigner-shaped H, twice (a few GB on the device)
+        hs = make_workload("jw_hh_n200_m6000")
+        g1, g2 = paulib.PauliSum.from_arrays(hs), paulib.PauliSum.from_arrays(hs)
+        for _ in range(2):
+            paulib.multiply(g1, g2, canonical=False).close()
+            o = paulib.multiply(g1, g2)
+            torch.cuda.synchronize()
+            if rank == 0:
+                print(json.dumps({"kernels_case": "jw_hh_n200_m6000", "distinct_out": o.n_terms}), flush=True)
+            o.close()
+        return
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     if args.only_propagation:
         # the gate, rotation and pair-product leg alone (for profiling its kernels)
-        stream = torch.cuda.current_stream()
-        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
-        hbm_peak, peak_src = measured_peaks()
         res = measure_propagation(paulib, stream, flush, max(3, args.steps), hbm_peak, peak_src)
         if rank == 0:
             print(json.dumps({"propagation": res}), flush=True)
         return
     if args.only_grouping:
-        # the grouping leg alone (for profiling its kernels); prints its object
-        stream = torch.cuda.current_stream()
         if rank == 0:
             print(json.dumps({"grouping": measure_grouping(paulib, stream, max(5, args.steps), gsizes)}), flush=True)
         return
 
     h = make_workload(args.workload)
     products = h.m * h.m
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    W = h.x.shape[0]
+    WP = 1
+    while WP < W:
+        WP *= 2
 
     # Two handles holding the same sum: the headline runs the general
     # ordered-pair product over all |H|^2 pairs.  multiply(gh, gh) with one
@@ -499,6 +672,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms = max_over_ranks(statistics.mean(step_ms), world, "cuda")
     value = job_rate(products, world, ms)
+    method = paulib.last_canon_method()
 
     # ---- the same product through one handle (symmetric pairs i <= j)
     for _ in range(2):
@@ -516,16 +690,24 @@ def run_ours(args):
     symmetric = {"ms_per_step": sms_, "value": products / (sms_ / 1e3), "speedup_vs_ordered": ms / sms_,
                  "pair_evaluations": h.m * (h.m + 1) // 2}
 
-    # ---- mixed precision on the same input (speed and error vs the FP64 result)
-    W = h.x.shape[0]
-    ref = paulib.multiply(gh, gh, "fp64")
-    rx = torch.empty((W, U), dtype=torch.int64, device="cuda")
-    rz = torch.empty_like(rx)
-    rc = torch.empty((U, 2), dtype=torch.float64, device="cuda")
-    ref.export(rx, rz, rc, None, stream=stream)
-    ref.close()
-    dx, dz, dc = torch.empty_like(rx), torch.empty_like(rz), torch.empty_like(rc)
-    rmag = torch.clamp(torch.linalg.vector_norm(rc, dim=1), min=1e-300)
+    # ---- mixed precision on the same input: speed, and each mode's merged
+    # coefficients against the FP64 oracle on sampled output strings
+    rng = np.random.default_rng(11)
+    pos = np.unique(rng.integers(0, U, 120))
+    sampled = {}
+
+    def sample_values(o, name):
+        vals = np.zeros(len(pos), np.complex128)
+        qx = np.zeros((W, len(pos)), np.uint64)
+        qz = np.zeros((W, len(pos)), np.uint64)
+        for t, p in enumerate(pos):
+            x, z, c, _ = o.export_range(int(p), 1)
+            qx[:, t], qz[:, t], vals[t] = x[:, 0], z[:, 0], c[0]
+        sampled[name] = (qx, qz, vals)
+
+    o, _, _ = step("fp64")
+    sample_values(o, "fp64")
+    o.close()
     precision = {}
     for prec in ("fp32_fp64merge", "fp32_twosum"):
         for _ in range(2):
@@ -539,96 +721,129 @@ def run_ours(args):
             tms.append(e0.elapsed_time(e1))
             if k == 0:
                 assert o.n_terms == U
-                o.export(dx, dz, dc, None, stream=stream)
-                assert torch.equal(dx, rx) and torch.equal(dz, rz), "mixed-precision key set differs"
-                err = torch.amax(torch.abs(dc - rc), dim=1)
-                # input |c| >= 1e-6, so a merged |c| below 1e-12 is (near) cancellation,
-                # where a relative error is meaningless; those get absolute errors only
-                nz = rmag > 1e-12
-                rel = (err[nz] / rmag[nz]).float()
-                srt = torch.sort(rel[:: max(1, int(nz.sum()) // 4_000_000)]).values
-                stats = {"max_abs_err_vs_fp64": float(err.max()),
-                         "max_abs_err_on_cancelled_terms": float(err[~nz].max()) if (~nz).any() else 0.0,
-                         "cancelled_terms": int((~nz).sum()),
-                         "max_rel_err_vs_fp64": float(rel.max()),
-                         "p99_rel_err_vs_fp64": float(srt[int(0.99 * (len(srt) - 1))]),
-                         "median_rel_err_vs_fp64": float(srt[(len(srt) - 1) // 2])}
+                sample_values(o, prec)
+                assert np.array_equal(sampled[prec][0], sampled["fp64"][0]), "mixed-precision key set differs"
             o.close()
         pm = statistics.mean(tms)
-        precision[prec] = dict(ms_per_step=pm, value=products / (pm / 1e3), speedup_vs_fp64=ms / pm, **stats)
-    del rx, rz, rc, dx, dz, dc, rmag
-    torch.cuda.empty_cache()  # the outer-product leg below needs the memory back
+        precision[prec] = {"ms_per_step": pm, "value": products / (pm / 1e3), "speedup_vs_fp64": ms / pm}
+    from oracle import pauli_oracle
+    qx, qz, _ = sampled["fp64"]
+    oc, oabs, _ = pauli_oracle.query_product_coeffs(h.n, h.as_tuple(), h.as_tuple(), qx, qz)
+    live = np.abs(oc) > 1e-12  # cancelled strings get absolute errors only
+    for name in ("fp64", "fp32_fp64merge", "fp32_twosum"):
+        c = sampled[name][2]
+        err = np.maximum(np.abs(c.real - oc.real), np.abs(c.imag - oc.imag))
+        sc = err / oabs
+        rel = err[live] / np.abs(oc[live])
+        stats = {"samples": int(len(pos)), "max_err_over_sum_abs": float(sc.max()),
+                 "p99_err_over_sum_abs": float(np.quantile(sc, 0.99)),
+                 "median_err_over_sum_abs": float(np.median(sc)), "max_abs_err": float(err.max()),
+                 "max_rel_err": float(rel.max()) if live.any() else 0.0,
+                 "median_rel_err": float(np.median(rel)) if live.any() else 0.0}
+        if name == "fp64":
+            precision["fp64_vs_oracle"] = stats
+        else:
+            precision[name]["error_vs_oracle"] = stats
+    torch.cuda.empty_cache()
 
-    # ---- end to end through the C ABI with host buffers
+    # ---- end to end through the C ABI with host buffers, on the same
+    # two-handle ordered-pair path as the headline
     hx = torch.from_numpy(h.x.view(np.int64)).pin_memory()
     hz = torch.from_numpy(h.z.view(np.int64)).pin_memory()
     hc = torch.from_numpy(h.c.view(np.float64)).pin_memory()
     ox = torch.empty((W, U), dtype=torch.int64).pin_memory()
     oz = torch.empty((W, U), dtype=torch.int64).pin_memory()
-    oc = torch.empty((U, 2), dtype=torch.float64).pin_memory()
+    oc_ = torch.empty((U, 2), dtype=torch.float64).pin_memory()
     e2e_ms = []
     for k in range(args.warmup + max(2, args.steps // 2)):
         flush.fill_(k)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        g = paulib.PauliSum.create(h.n, hx, hz, hc, stream=stream)
-        o = paulib.multiply(g, g, "fp64")
-        o.export(ox, oz, oc, None, stream=stream)
+        g1 = paulib.PauliSum.create(h.n, hx, hz, hc, stream=stream)
+        g2 = paulib.PauliSum.create(h.n, hx, hz, hc, stream=stream)
+        o = paulib.multiply(g1, g2, "fp64")
+        o.export(ox, oz, oc_, None, stream=stream)
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) * 1e3
         if k >= args.warmup:
             e2e_ms.append(dt)
         o.close()
-        g.close()
+        g1.close()
+        g2.close()
     e2e = max_over_ranks(statistics.mean(e2e_ms), world, "cuda")
-    h2d = hx.numel() * 8 + hz.numel() * 8 + hc.numel() * 8
-    d2h = (ox.numel() + oz.numel() + oc.numel()) * 8
+    h2d = 2 * (hx.numel() * 8 + hz.numel() * 8 + hc.numel() * 8)
+    d2h = (ox.numel() + oz.numel() + oc_.numel()) * 8
+    del ox, oz, oc_
 
-    # ---- roofline of the dominant stage: compulsory HBM bytes that stage
-    # must move per step, over the stage's device time (CUDA events recorded
-    # on the launching stream around the stage's kernels)
-    hbm_peak, peak_src = measured_peaks()
+    # ---- roofline of the dominant stage (the kernels of the stage that takes
+    # most device time), from CUDA events recorded on the launching stream
+    peaks = paulib.measure_peaks(stream)
     dom = max(stage_ms, key=lambda s: stage_ms[s])
     dom_ms = stage_ms[dom] / args.steps
-    WP = 1
-    while WP < W:
-        WP *= 2
     term_bytes = 16 * WP + 16 + 1  # key words, complex128, phase byte
     stage_bytes = {
-        "count": products * 2,                       # one bucket id per product
-        "scatter": products * (2 + 4),               # bucket id in, record out
+        "count": products * 2,                       # one coarse range id per product
+        "scatter": products * (2 + 4),               # range id in, record out
         "level2": products * (4 + 2 + 4),            # one split pass: record in, child id, record out
-        "leaf": products * 4 + U * term_bytes,       # records in, merged terms out
-        "compact": products + U * (term_bytes + 16 * WP + 16),  # flags, staged terms in, terms out
+        "leaf": products * 4 + U * (16 * WP + 16),   # records in, merged terms out (staged)
+        "compact": products + U * (2 * (16 * WP + 16) + 1),  # flags, staged terms in, terms out
+        "split": products * (4 + 2),                 # slot sort: records in, slot ids out
+        "place": products * (4 + 2 + 16 * WP + 16),  # records and slot ids in, terms out
     }
     bytes_per = stage_bytes.get(dom, products * 4)
+    kernels = {"leaf": "k_leaf_warp + k_leaf_block", "level2": "k_level2", "count": "k_count_prod",
+               "scatter": "k_scatter", "compact": "k_flag_count + k_compact", "split": "k_slot_split + k_slot_locate",
+               "place": "k_slot_place"}
     roof = {"bound": "hbm", "achieved": bytes_per / (dom_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-            "peak_source": peak_src, "kernel": dom, "bytes_per_step": bytes_per}
+            "peak_source": peak_src, "stage": dom, "kernel": kernels.get(dom, dom), "bytes_per_step": bytes_per,
+            "kernel_ms_per_step": dom_ms}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = TRAFFIC_PER_PRODUCT.get((dom, h.n)) and TRAFFIC_PER_PRODUCT[(dom, h.n)] * products
+    tpp, src_hash = traffic_per_product(dom, h.n)
+    roof["traffic"] = tpp * products if tpp is not None else None
+    roof["traffic_source"] = ("profiles/traffic.json (ncu, pipeline source %s)" % src_hash) if tpp is not None \
+        else "none for the current pipeline source"
     if dom in ("leaf", "level2"):
         # these stages gather both factors' key words (and, in the leaf, the
-        # coefficients) from L2-resident tables: bound by L2 gathers and latency
+        # coefficients) from L2-resident tables, once per record per pass
         gathered = products * 2 * (16 * WP + (16 if dom == "leaf" else 0))
+        l2 = peaks["l2_gather64_bytes_per_s"] / 1e9
         roof["l2_gather_bytes"] = gathered
         roof["l2_gather_GBs"] = gathered / (dom_ms / 1e3) / 1e9
-    roof["kernel_ms_per_step"] = dom_ms
-    roof["stage_ms_per_step"] = {k: v / args.steps for k, v in stage_ms.items()}
-    # whole-step bound of the method (compulsory traffic only: inputs once,
-    # merged terms once; the sort's intermediate traffic is overhead)
+        roof["l2_gather_peak_GBs"] = l2
+        roof["l2_gather_frac"] = roof["l2_gather_GBs"] / l2
+    roof["stage_ms_per_step"] = {k: v / args.steps for k, v in stage_ms.items() if v}
+    # whole-step bound of the method: compulsory traffic (inputs once, merged
+    # terms once; the sort's intermediate traffic is overhead), the FP64
+    # work (per product: complex product 2 MUL + 2 FMA, merge 2 ADD) and the
+    # integer work of key and phase (per product: 2*WP 64-bit XOR + the
+    # bit-sliced |x&z| counter, about 6*WP three-input logic ops on 32-bit
+    # halves, and 4 population counts), each over its measured pipe rate
     t_hbm = (2 * h.m * term_bytes + U * term_bytes) / (hbm_peak * 1e9)
-    t_fp = products * 8 / (FP64_PEAK_TFLOPS * 1e12)
-    roof["step_bound_ms"] = 1e3 * max(t_hbm, t_fp)
-    roof["step_frac"] = roof["step_bound_ms"] / ms
+    t_fp64 = products * 6 / peaks["fp64_fma_per_s"]
+    t_int = products * 6 * WP / peaks["lop3_per_s"]
+    t_popc = products * 4 / peaks["popc_per_s"]
+    bounds = {"hbm": t_hbm, "fp64": t_fp64, "int": t_int, "popc": t_popc}
+    roof["step_bound_ms"] = {k: 1e3 * v for k, v in bounds.items()}
+    roof["step_binding"] = max(bounds, key=bounds.get)
+    roof["step_frac"] = 1e3 * max(bounds.values()) / ms
+    roof["pipe_peaks"] = peaks
 
     outer = measure_outer_product(paulib, gh, gh2, h, stream, flush, max(2, args.steps // 2), hbm_peak, peak_src)
+    gh.close()
+    gh2.close()
+    tiny = measure_tiny(paulib, stream)
+    workloads = {"tiny": tiny}
+    if not args.no_streaming:
+        workloads["streaming"] = measure_streaming(paulib, stream, hbm_peak)
+    if args.workload != "jw_hh_n100_m20000" and not args.no_n100:
+        workloads["jw_hh_n100_m20000"] = measure_hh(paulib, "jw_hh_n100_m20000", stream, flush,
+                                                   max(3, args.steps // 2), 2)
     batched = None
     if not args.no_batched:
         batched = measure_batched(paulib, stream, flush, max(3, args.steps // 2))
     propagation = None
     if not args.no_propagation:
         propagation = measure_propagation(paulib, stream, flush, max(3, args.steps // 2), hbm_peak, peak_src)
-
     grouping = None
     if not args.no_grouping:
         grouping = measure_grouping(paulib, stream, max(5, args.steps), gsizes)
@@ -638,19 +853,19 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "n_qubits": h.n, "terms": h.m, "products": products,
                        "distinct_out": U, "parallelism": "replicas" if world > 1 else "single",
+                       "canonical_method": "range sort" if method[0] == 1 else "slot sort",
                        "l2": "512 MiB flush between timed steps"},
             "roofline": roof, "outer_product": outer, "precision": precision, "symmetric": symmetric,
-            "batched": batched, "propagation": propagation, "grouping": grouping,
+            "workloads": workloads, "batched": batched, "propagation": propagation, "grouping": grouping,
             "e2e": {"value": job_rate(products, world, e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e,
+                    "path": "two handles created from pinned host buffers, ordered-pair product, export"},
             "gpu_launches": int(sum(stage_launches.values())),
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_rate(h)[0]
+        line["cpu_baseline"] = oracle_baselines(h)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    gh.close()
-    gh2.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -671,6 +886,13 @@ def main():
     ap.add_argument("--only-propagation", action="store_true", help="run the gate, rotation and pair-product leg alone")
     ap.add_argument("--grouping-sizes", default="200,500,1000,2000,20000",
                     help="term counts of the grouping leg (comma separated)")
+    ap.add_argument("--no-streaming", action="store_true", help="skip the 1M-term x 256-string streaming leg")
+    ap.add_argument("--no-n100", action="store_true", help="skip the n=100 H*H leg")
+    ap.add_argument("--peaks", action="store_true", help="print the measured pipe rates and exit")
+    ap.add_argument("--kernels-case", action="store_true",
+                    help="run the small kernel-profiling case (raw and canonical H*H, n=200, 6,000 terms) and exit")
+    ap.add_argument("--method", type=int, default=-1,
+                    help="canonicalisation method (0 slot sort, 1 range sort; -1: library default)")
     ap.add_argument("--coarse-factor", type=int, default=0,
                     help="first-level fan-out of the canonicalisation (0: library default); for profiling "
                          "small cases with the range mix of large ones")

@@ -257,6 +257,18 @@ paulib_status paulib_set_slot_tuning(int32_t key_words, int32_t method, int32_t 
  * Errors: INVALID_ARG for NULL pointers.                                    */
 paulib_status paulib_last_canon_method(int32_t* method, int32_t* fallback_bits);
 
+/* Measured rates of the pipes this path uses (no counterpart in the paper),
+ * for roofline denominators; each from a microbenchmark of independent
+ * dependency chains on every SM, timed with CUDA events on `stream`:
+ *   out[0] FP64 fused multiply-adds/s, out[1] FP32 fused multiply-adds/s,
+ *   out[2] 32-bit three-input logic operations/s (64-bit and-xor chains),
+ *   out[3] 32-bit integer adds/s, out[4] population counts/s,
+ *   out[5] bytes/s of random 64-byte reads from a 4 MiB (L2-resident) table,
+ *   out[6] the same for 32-byte reads.
+ * Writes min(n, 7) values; takes about a second.  Synchronises `stream`.
+ * Errors: INVALID_ARG (NULL or n < 1), OOM, CUDA.                            */
+paulib_status paulib_measure_peaks(double* out, int32_t n, void* stream);
+
 /* Test settings (no counterpart in the paper; 0 turns a setting off, the
  * default).  Results never depend on them except as stated.
  *   knob 1, value 1..63: the range sort's warp leaves keep only the low

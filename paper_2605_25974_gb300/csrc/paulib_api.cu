@@ -883,6 +883,14 @@ paulib_status paulib_set_slot_tuning(int32_t key_words, int32_t method, int32_t 
     PAULIB_API_END
 }
 
+paulib_status paulib_measure_peaks(double* out, int32_t n, void* stream) {
+    PAULIB_API_BEGIN
+    if (!out || n < 1) fail(PAULIB_ERR_INVALID_ARG, "out must hold at least one value");
+    measure_peaks(out, n, (cudaStream_t)stream);
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
 paulib_status paulib_set_debug(int32_t knob, int64_t value) {
     PAULIB_API_BEGIN
     if (knob == 1) {

@@ -187,6 +187,9 @@ void apply_clifford(paulib_sum* s, int32_t nops, const int32_t* ops_host, cudaSt
 paulib_sum* rotate(const paulib_sum* s, const uint64_t* pk_host, double theta, double threshold, int mode,
                    cudaStream_t st);
 
+// Pipe microbenchmarks (paulib_measure_peaks).
+void measure_peaks(double* out, int n, cudaStream_t st);
+
 // Allocation-free canonical product using the library's static scratch
 // array (see paulib_multiply_noalloc in include/paulib.h).
 void multiply_noalloc(int32_t n_qubits, int64_t na, const uint64_t* a_x, const uint64_t* a_z,

@@ -29,7 +29,8 @@ EXPORTED = ["paulib_abi_version", "paulib_sum_create", "paulib_sum_info", "pauli
             "paulib_batch_plan_outputs", "paulib_batch_plan_destroy", "paulib_set_tuning",
             "paulib_apply_clifford", "paulib_rotate", "paulib_multiply_pairwise",
             "paulib_group_commuting", "paulib_set_group_candidates", "paulib_set_slot_tuning",
-            "paulib_last_canon_method", "paulib_sum_export_range", "paulib_last_canon_stats", "paulib_set_debug"]
+            "paulib_last_canon_method", "paulib_sum_export_range", "paulib_last_canon_stats", "paulib_set_debug",
+            "paulib_measure_peaks"]
 GATES = {"h": 0, "s": 1, "cnot": 2, "cz": 3}
 STAGES = ["convert", "sample", "count", "scatter", "level2", "compact", "raw", "export", "leaf", "group", "split",
           "place"]
@@ -107,6 +108,8 @@ def load(path: Optional[str] = None):
     lib.paulib_last_canon_stats.restype = _i32
     lib.paulib_set_debug.argtypes = [_i32, _i64]
     lib.paulib_set_debug.restype = _i32
+    lib.paulib_measure_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), _i32, _vp]
+    lib.paulib_measure_peaks.restype = _i32
     for name in ("paulib_sum_create", "paulib_sum_info", "paulib_sum_export", "paulib_multiply",
                  "paulib_compress", "paulib_multiply_batched", "paulib_set_allocator"):
         getattr(lib, name).restype = _i32
@@ -360,6 +363,17 @@ def last_canon_method():
     m, b = _i32(), _i32()
     _check(load().paulib_last_canon_method(ctypes.byref(m), ctypes.byref(b)))
     return int(m.value), int(b.value)
+
+
+PEAK_NAMES = ("fp64_fma_per_s", "fp32_fma_per_s", "lop3_per_s", "iadd_per_s", "popc_per_s",
+              "l2_gather64_bytes_per_s", "l2_gather32_bytes_per_s")
+
+
+def measure_peaks(stream=None):
+    """Measured pipe rates (dict, see paulib_measure_peaks)."""
+    v = (ctypes.c_double * len(PEAK_NAMES))()
+    _check(load().paulib_measure_peaks(v, len(PEAK_NAMES), _vp(_stream(stream))))
+    return dict(zip(PEAK_NAMES, [float(q) for q in v]))
 
 
 def set_debug(knob, value):
