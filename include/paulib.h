@@ -134,8 +134,11 @@ paulib_status paulib_compress(const paulib_sum* in, int32_t precision, void* str
                               paulib_sum** out);
 
 /* `batch` independent canonical products out[b] = canonical(a[b] * b[b]).
- * All operands must share one qubit count.  Products are processed together
- * as one canonicalisation of keys prefixed by the problem index.            */
+ * All operands must share one qubit count.  When every right operand has at
+ * most 64 terms, one persistent kernel computes every product: its CTAs take
+ * problems largest first and write each canonical sum directly.  Otherwise
+ * all products go through one canonicalisation of keys prefixed by the
+ * problem index.  Both give the same sums.                                  */
 paulib_status paulib_multiply_batched(int32_t batch, const paulib_sum* const* a,
                                       const paulib_sum* const* b, int32_t precision, void* stream,
                                       paulib_sum** out);
@@ -143,9 +146,10 @@ paulib_status paulib_multiply_batched(int32_t batch, const paulib_sum* const* a,
 /* Batched plan: the same batched canonical product, prepared once and then
  * launched any number of times without allocating or synchronising, so a
  * launch can be captured in a CUDA graph and replayed (e.g. one graph per
- * Pauli-propagation step shape).  All problems are canonicalised together:
- * the sort key is (problem index, string key), so one sample sort serves
- * every problem and outputs come out grouped by problem.
+ * Pauli-propagation step shape).  The method is chosen at creation as for
+ * paulib_multiply_batched: the persistent kernel (one launch after three
+ * memsets) when every right operand has at most 64 terms, else the general
+ * pipeline.
  *   create: validates the operands, sizes every buffer from |A_b|, |B_b| (each
  *     output's capacity is |A_b|*|B_b|) and runs the product once to lay out
  *     its workspace.  The operands must stay alive and unchanged while the
@@ -215,13 +219,16 @@ paulib_status paulib_multiply_noalloc(int32_t n_qubits, int64_t na, const uint64
  * every size).  No counterpart in the paper; results never depend on it.
  *   coarse_factor: a first-level key range targets coarse_factor x the
  *       shared-memory leaf capacity records (2..256, default 32);
- *   oversample: splitter sample size per first-level range (4..128, default 32);
- *   count_ctas_per_sm: CTAs per SM of the first-level counting kernel (1..16);
+ *   oversample: splitter sample size per first-level range (4..128, default 64);
+ *   count_ctas_per_sm: CTAs per SM of the first-level counting kernel (1..16,
+ *       default 8);
  *   range_ctas_per_sm: CTAs per SM of the range sort/merge kernel (1..2).
  * A value <= 0 keeps the current setting.  If the environment variable
  * PAULIB_TUNE_FILE names a file when the library first needs a setting, its
  * lines "key_words coarse_factor oversample count_ctas_per_sm
- * range_ctas_per_sm" are applied first (the file the autotuner writes).     */
+ * range_ctas_per_sm [method leaf_cap slot_target slot_oversample]" are
+ * applied first (the file the autotuner writes); the four optional fields
+ * are those of paulib_set_slot_tuning (0 = built-in default).               */
 paulib_status paulib_set_tuning(int32_t key_words, int32_t coarse_factor, int32_t oversample,
                                 int32_t count_ctas_per_sm, int32_t range_ctas_per_sm);
 
@@ -277,6 +284,13 @@ paulib_status paulib_measure_peaks(double* out, int32_t n, void* stream);
  *   knob 2, value 1..4096: a range CTA's worklist holds `value` entries; a
  *     split that needs more sets the device error word and returns, and the
  *     call fails with PAULIB_ERR_INTERNAL (no result).
+ *   knob 3, value 1: batched products and batch plans made afterwards take
+ *     the general multi-kernel pipeline even where the persistent kernel
+ *     applies (the same result).
+ *   knob 4, value 32..2048: leaf capacity of the persistent batched kernel
+ *     for plans made afterwards (at most its compiled capacity: 1024 records
+ *     up to 8-word keys, 512 for 16-word, 256 for 32-word keys); a small
+ *     capacity makes small problems take its split path (the same result).
  * Errors: INVALID_ARG for an unknown knob or a value out of range.          */
 paulib_status paulib_set_debug(int32_t knob, int64_t value);
 

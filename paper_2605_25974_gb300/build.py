@@ -15,7 +15,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpaulib.so")
 SOURCES = ["paulib_api.cu", "paulib_convert.cu", "paulib_canon.cu", "paulib_compress.cu", "paulib_batch.cu",
            "paulib_gates.cu", "paulib_group.cu", "paulib_peaks.cu"]
-HEADERS = ["paulib_device.cuh", "paulib_internal.h", "paulib_pipeline.cuh", "paulib_slots.cuh"]
+HEADERS = ["paulib_device.cuh", "paulib_internal.h", "paulib_pipeline.cuh", "paulib_slots.cuh", "paulib_persist.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -321,10 +321,13 @@ void load_tune_file_locked() {
     while (std::fgets(line, sizeof line, f)) {
         int kw = 0;
         Tuning t{0, 0, 0, 0};
+        SlotTuning st;
         if (line[0] == '#') continue;
-        if (std::sscanf(line, "%d %d %d %d %d", &kw, &t.coarse_factor, &t.oversample, &t.count_ctas_per_sm,
-                        &t.range_ctas_per_sm) == 5)
-            set_tuning_locked(kw, t);
+        const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d %d", &kw, &t.coarse_factor, &t.oversample,
+                                    &t.count_ctas_per_sm, &t.range_ctas_per_sm, &st.method, &st.leaf_cap,
+                                    &st.target, &st.oversample);
+        if (got >= 5) set_tuning_locked(kw, t);
+        if (got == 9 && (st.method == 0 || st.method == 1)) set_slot_tuning(kw, st, false);
     }
     std::fclose(f);
 }
@@ -353,6 +356,10 @@ thread_local int g_canon_bits = 0;
 }  // namespace
 
 SlotTuning slot_tuning_for(int key_words) {
+    {
+        std::lock_guard<std::mutex> lt(g_tune_mu);  // the tune file may set it
+        load_tune_file_locked();
+    }
     std::lock_guard<std::mutex> lk(g_slot_mu);
     for (const auto& kv : g_slot_by_words)
         if (kv.first == key_words) return kv.second;
@@ -388,6 +395,8 @@ void set_debug(int knob, int64_t value) {
     std::lock_guard<std::mutex> lk(g_debug_mu);
     if (knob == 1) g_debug.hash_bits = (int)value;
     else if (knob == 2) g_debug.stack_cap = (int)value;
+    else if (knob == 3) g_debug.batch_general = (int)value;
+    else if (knob == 4) g_debug.persist_leaf = (int)value;
 }
 
 void note_canon_method(int method, int bits) {
@@ -897,6 +906,11 @@ paulib_status paulib_set_debug(int32_t knob, int64_t value) {
         if (value < 0 || value > 64) fail(PAULIB_ERR_INVALID_ARG, "hash bits must be 0..64");
     } else if (knob == 2) {
         if (value < 0 || value > 4096) fail(PAULIB_ERR_INVALID_ARG, "stack capacity must be 0..4096");
+    } else if (knob == 3) {
+        if (value < 0 || value > 1) fail(PAULIB_ERR_INVALID_ARG, "batched method setting must be 0 or 1");
+    } else if (knob == 4) {
+        if (value != 0 && (value < 32 || value > 2048))
+            fail(PAULIB_ERR_INVALID_ARG, "persistent leaf capacity must be 0 or 32..2048");
     } else {
         fail(PAULIB_ERR_INVALID_ARG, "unknown debug setting " + std::to_string(knob));
     }

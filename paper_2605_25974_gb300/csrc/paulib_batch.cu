@@ -1,35 +1,20 @@
 // paulib_batch.cu -- batched canonical products and the prepared, graph-
 // capturable batch plan; the pipeline is in paulib_pipeline.cuh.
-#include "paulib_pipeline.cuh"
+#include "paulib_persist.cuh"
 
 namespace paulib {
 
 // ---------------------------------------------------------------- batched products
 //
-// Many independent products canonicalised together.  Problem b's records are
-// the global record range [r0s[b], r0s[b+1]); its products' keys are prefixed
-// by two words (b, 0), so the pipeline's single sort keeps problems apart and
-// emits them in order.  The output of problem b is then copied into its own
-// sum (capacity |A_b||B_b|).
-
-struct ProbDesc {
-    const uint64_t* ak;
-    const uint64_t* bk;
-    const uint8_t* ap;
-    const uint8_t* bp;
-    const void* ac;
-    const void* bc;
-    uint32_t na, nb;
-    uint64_t pad;
-};
-static_assert(sizeof(ProbDesc) == 64, "descriptor is one 64-byte record");
-
-struct OutDesc {
-    uint64_t* keys;
-    double2* coef;
-    uint8_t* pbase;
-    uint64_t pad;
-};
+// Many independent products canonicalised together.  Two methods give the
+// same sums:
+//   * the persistent kernel (paulib_persist.cuh), when every right operand
+//     has at most kPNB terms: one launch, one CTA per problem at a time;
+//   * the general pipeline otherwise: problem b's records are the global
+//     record range [r0s[b], r0s[b+1]); its products' keys are prefixed by two
+//     words (b, 0), so one sort keeps problems apart and emits them in order,
+//     and the output of problem b is then copied into its own sum.
+// Either way problem b's output sum has capacity |A_b||B_b|.
 
 template <int WP_, int MODE>
 struct BatchSrc {
@@ -162,9 +147,39 @@ struct paulib_batch_plan {
     unsigned long long* d_counts = nullptr;
     uint64_t* d_pstart = nullptr;
     int32_t* d_err = nullptr;
+    uint32_t* d_order = nullptr;  // problems by decreasing |A_b||B_b| (persistent kernel)
+    uint32_t* d_ticket = nullptr;
+    bool persist = false;
+    uint32_t leaf_cap = 0;  // 0: the compiled capacity
+    int ctas_per_sm = 2;
 };
 
 namespace paulib {
+
+template <int WP, int MODE>
+static void persist_launch(paulib_batch_plan* p, cudaStream_t st) {
+    constexpr int NW = 2 * WP;
+    using Lay = PLayout<WP, MODE>;
+    auto kern = k_batch_persist<WP, MODE>;
+    smem_attr(kern, Lay::BYTES);
+    int per_sm = 0;
+    if (!capture_safe())
+        check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, Lay::BYTES), "occupancy");
+    if (per_sm > 0) p->ctas_per_sm = per_sm;
+    const uint32_t grid = (uint32_t)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)p->batch, (int64_t)device_sm_count() * std::max(1, p->ctas_per_sm)));
+    Scratch bufs((size_t)p->R * 9, st);  // two record buffers and a child byte per record
+    Scratch levels((size_t)grid * persist_depth<NW>() * sizeof(PLevel), st);
+    StageScope ss(ST_LEAF, st);
+    check_cuda(cudaMemsetAsync(p->d_ticket, 0, 4, st), "memset ticket");
+    kern<<<grid, kPThreads, Lay::BYTES, st>>>(p->d_probs, p->d_outs, p->d_order, p->d_r0s, (uint32_t)p->batch,
+                                              bufs.as<uint32_t>(), bufs.as<uint32_t>() + p->R,
+                                              reinterpret_cast<uint8_t*>(bufs.as<uint32_t>() + 2 * p->R),
+                                              levels.as<PLevel>(), p->d_ticket, p->d_counts, p->d_err,
+                                              p->leaf_cap);
+    note_launch(ST_LEAF);
+    check_cuda(cudaGetLastError(), "k_batch_persist");
+}
 
 template <int WP, int MODE>
 static void batch_launch_impl(paulib_batch_plan* p, cudaStream_t st) {
@@ -173,6 +188,10 @@ static void batch_launch_impl(paulib_batch_plan* p, cudaStream_t st) {
     check_cuda(cudaMemsetAsync(p->d_counts, 0, (size_t)p->batch * 8, st), "memset counts");
     check_cuda(cudaMemsetAsync(p->d_err, 0, 4, st), "memset err");
     if (p->R == 0) return;
+    if (p->persist) {
+        persist_launch<WP, MODE>(p, st);
+        return;
+    }
     Src src{p->d_probs, p->d_r0s, (uint32_t)p->batch};
     Staged sg;
     run_pipeline<Src, MODE>(src, (uint32_t)p->R, 0, st, sg);
@@ -251,7 +270,8 @@ paulib_batch_plan* batch_plan_create(int32_t batch, const paulib_sum* const* a, 
         const size_t szO = (size_t)batch * sizeof(OutDesc);
         const size_t szC = ((size_t)batch * 8 + 255) / 256 * 256;
         const size_t szS = ((size_t)(batch + 1) * 8 + 255) / 256 * 256;
-        const size_t total = szP + szR + szO + szC + szS + 256;
+        const size_t szQ = ((size_t)batch * 4 + 255) / 256 * 256;
+        const size_t total = szP + szR + szO + szC + szS + 256 + szQ + 256;
         p->desc = dev_alloc(total, st);
         char* base = static_cast<char*>(p->desc);
         p->d_probs = reinterpret_cast<ProbDesc*>(base);
@@ -260,6 +280,20 @@ paulib_batch_plan* batch_plan_create(int32_t batch, const paulib_sum* const* a, 
         p->d_counts = reinterpret_cast<unsigned long long*>(base + szP + szR + szO);
         p->d_pstart = reinterpret_cast<uint64_t*>(base + szP + szR + szO + szC);
         p->d_err = reinterpret_cast<int32_t*>(base + szP + szR + szO + szC + szS);
+        p->d_order = reinterpret_cast<uint32_t*>(base + szP + szR + szO + szC + szS + 256);
+        p->d_ticket = reinterpret_cast<uint32_t*>(base + szP + szR + szO + szC + szS + 256 + szQ);
+        // the persistent kernel takes the batch when every right operand fits
+        // its shared memory; problems go largest first
+        const DebugSettings dbg = debug_settings();
+        p->persist = dbg.batch_general == 0;
+        for (int32_t q = 0; q < batch && p->persist; ++q)
+            if ((uint64_t)b[q]->n_terms > kPNB) p->persist = false;
+        p->leaf_cap = dbg.persist_leaf > 0 ? (uint32_t)dbg.persist_leaf : 0u;
+        std::vector<uint32_t> order(batch);
+        for (int32_t q = 0; q < batch; ++q) order[q] = (uint32_t)q;
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+            return (uint64_t)(r0s[x + 1] - r0s[x]) > (uint64_t)(r0s[y + 1] - r0s[y]);
+        });
         std::vector<ProbDesc> hp(batch);
         std::vector<OutDesc> ho(batch);
         std::vector<F32Job> jobs;
@@ -276,7 +310,7 @@ paulib_batch_plan* batch_plan_create(int32_t batch, const paulib_sum* const* a, 
             d.bp = b[q]->pbase;
             d.na = (uint32_t)a[q]->n_terms;
             d.nb = (uint32_t)b[q]->n_terms;
-            d.pad = 0;
+            d.na_inv = recip64(d.na);
             if (mode == M_FP64) {
                 d.ac = a[q]->coef;
                 d.bc = b[q]->coef;
@@ -293,6 +327,8 @@ paulib_batch_plan* batch_plan_create(int32_t batch, const paulib_sum* const* a, 
         check_cuda(cudaMemcpyAsync(p->d_probs, hp.data(), szP, cudaMemcpyHostToDevice, st), "desc copy");
         check_cuda(cudaMemcpyAsync(p->d_r0s, r0s.data(), (size_t)(batch + 1) * 4, cudaMemcpyHostToDevice, st), "r0 copy");
         check_cuda(cudaMemcpyAsync(p->d_outs, ho.data(), szO, cudaMemcpyHostToDevice, st), "out copy");
+        check_cuda(cudaMemcpyAsync(p->d_order, order.data(), (size_t)batch * 4, cudaMemcpyHostToDevice, st),
+                   "order copy");
         Scratch jobs_d;
         if (!jobs.empty()) {
             jobs_d = Scratch(jobs.size() * sizeof(F32Job), st);

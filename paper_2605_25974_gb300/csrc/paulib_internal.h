@@ -84,8 +84,8 @@ int padded_words(int W);
 // Pipeline tuning (paulib_set_tuning); never changes results.
 struct Tuning {
     int coarse_factor = 32;
-    int oversample = 32;
-    int count_ctas_per_sm = 4;
+    int oversample = 64;
+    int count_ctas_per_sm = 8;
     int range_ctas_per_sm = 2;
 };
 Tuning tuning_for(int key_words);
@@ -94,10 +94,14 @@ void set_tuning(int key_words, const Tuning& t);
 // Test settings (paulib_set_debug); 0 = off.  hash_bits: keep only the low
 // hash_bits bits of the range sort's warp-leaf key hashes (forces the
 // hash-clash path); stack_cap: entries of a range CTA's worklist (a small cap
-// makes the split raise its stack error and return).
+// makes the split raise its stack error and return); batch_general: batch
+// plans made afterwards use the general pipeline; persist_leaf: a smaller
+// leaf for the persistent batched kernel (more splits on small inputs).
 struct DebugSettings {
     int hash_bits = 0;
     int stack_cap = 0;
+    int batch_general = 0;  // batch plans take the general pipeline
+    int persist_leaf = 0;   // leaf capacity of the persistent batched kernel
 };
 DebugSettings debug_settings();
 void set_debug(int knob, int64_t value);

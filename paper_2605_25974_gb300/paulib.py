@@ -298,25 +298,6 @@ class BatchPlan:
         _check(load().paulib_batch_plan_outputs(_vp(self._h), _vp(_stream(stream)), O))
         return [_Borrowed(O[i]) for i in range(self.batch)]
 
-    def export_range(self, first, count, stream=None, with_phase=False):
-        """Copies terms [first, first + count) out into new host arrays."""
-        W = self.words
-        x = np.zeros((W, count), np.uint64)
-        z = np.zeros((W, count), np.uint64)
-        c = np.zeros(count, np.complex128)
-        k = np.zeros(count, np.uint8) if with_phase else None
-        st = _stream(stream)
-        _check(load().paulib_sum_export_range(_vp(self._h), ctypes.c_int64(first), ctypes.c_int64(count), _ptr(x),
-                                              _ptr(z), _ptr(c), _ptr(k), _vp(st)))
-        import torch
-        if stream is None:
-            torch.cuda.current_stream().synchronize()
-        elif hasattr(stream, "synchronize"):
-            stream.synchronize()
-        else:
-            torch.cuda.synchronize()
-        return x, z, c, k
-
     def close(self):
         if self._h:
             load().paulib_batch_plan_destroy(_vp(self._h))

@@ -133,6 +133,6 @@ def test_hash_clash_path_of_the_warp_leaves(lib, oracle, bits):
 
 
 def test_debug_argument_checks(lib):
-    for knob, value in ((0, 1), (3, 1), (1, 65), (1, -1), (2, 5000)):
+    for knob, value in ((0, 1), (5, 1), (1, 65), (1, -1), (2, 5000)):
         with pytest.raises(lib.PaulibError, match="INVALID_ARG"):
             lib.set_debug(knob, value)
