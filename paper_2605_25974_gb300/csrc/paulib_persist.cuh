@@ -306,34 +306,125 @@ __device__ __forceinline__ int pleaf_cmp(const uint64_t* keys, const uint64_t* c
     return 0;
 }
 
-// Bitonic sort of the leaf's (window, slot) pairs by pleaf_cmp, then record
-// number; npow (a power of two, at least n) positions, padding last.
+// A leaf sort entry: window and slot.
+struct PE {
+    uint64_t c;
+    uint32_t s;
+};
+
+// Strict order of two leaf entries: padding (slot >= n) last, then by
+// window, by whole key from word w0 on, by record number and by slot.
 template <int NW, uint32_t CAP>
-__device__ __forceinline__ void psort_leaf(const uint64_t* keys, uint64_t* c1, uint16_t* idx, const uint32_t* rr,
-                                           uint32_t npow, uint32_t n, uint32_t w0) {
-    for (uint32_t k = 2; k <= npow; k <<= 1) {
+__device__ __forceinline__ bool pe_gt(const PE& a, const PE& b, const uint64_t* keys, const uint32_t* rr, uint32_t n,
+                                      uint32_t w0) {
+    const bool pa = a.s >= n, pb = b.s >= n;
+    if (pa || pb) return pa && (!pb || a.s > b.s);
+    if (a.c != b.c) return a.c > b.c;
+    for (uint32_t w = w0; w < (uint32_t)NW; ++w) {
+        const uint64_t ka = keys[(size_t)w * CAP + a.s], kb = keys[(size_t)w * CAP + b.s];
+        if (ka != kb) return ka > kb;
+    }
+    const uint32_t ra = rr[a.s], rb = rr[b.s];
+    return ra != rb ? ra > rb : a.s > b.s;
+}
+
+// Bitonic sort of the first np positions (a power of two, 32 .. 256E) held
+// in registers: position g = warp * 32E + e * 32 + lane.  Partners closer
+// than 32 are exchanged by shuffles, partners 32 .. 16E apart between a
+// thread's own rows, the rest through shared memory (sc, si), so only the
+// stages that cross warps need barriers.  Positions >= np never meet a
+// position below np and stay where they are.
+template <int NW, uint32_t CAP, uint32_t E>
+__device__ __forceinline__ void psort_reg(PE (&x)[E], uint32_t np, uint64_t* sc, uint16_t* si, const uint64_t* keys,
+                                          const uint32_t* rr, uint32_t n, uint32_t w0) {
+    const uint32_t lane = threadIdx.x & 31u, wb = (threadIdx.x >> 5) * 32u * E;
+    const bool active = wb < np;  // whole warps lie below np or at or above it
+#pragma unroll 1
+    for (uint32_t k = 2; k <= np; k <<= 1) {
+#pragma unroll 1
         for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t q = threadIdx.x; q < npow / 2; q += kPThreads) {
-                const uint32_t i = ((q & ~(j - 1u)) << 1) | (q & (j - 1u));
-                const uint32_t l = i | j;
-                int c = pleaf_cmp<NW, CAP>(keys, c1, idx, i, l, n, w0);
-                if (c == 0) {
-                    const uint32_t a = idx[i], b = idx[l];
-                    const uint32_t ra = a < n ? rr[a] : 0xffffffffu, rb = b < n ? rr[b] : 0xffffffffu;
-                    c = ra != rb ? (ra < rb ? -1 : 1) : (a < b ? -1 : 1);
+            if (j >= 32u * E) {
+#pragma unroll
+                for (uint32_t e = 0; e < E; ++e) {
+                    const uint32_t g = wb + e * 32u + lane;
+                    if (g < np) {
+                        sc[g] = x[e].c;
+                        si[g] = (uint16_t)x[e].s;
+                    }
                 }
-                if ((c > 0) == ((i & k) == 0)) {
-                    const uint64_t t1 = c1[i];
-                    c1[i] = c1[l];
-                    c1[l] = t1;
-                    const uint16_t t2 = idx[i];
-                    idx[i] = idx[l];
-                    idx[l] = t2;
+                __syncthreads();
+#pragma unroll
+                for (uint32_t e = 0; e < E; ++e) {
+                    const uint32_t g = wb + e * 32u + lane, p = g ^ j;
+                    if (g < np) {
+                        const PE y{sc[p], si[p]};
+                        const bool keep_min = ((g & j) == 0) == ((g & k) == 0);
+                        if (keep_min == pe_gt<NW, CAP>(x[e], y, keys, rr, n, w0)) x[e] = y;
+                    }
+                }
+                __syncthreads();
+            } else if (active) {
+                if (j >= 32u) {
+                    const uint32_t d = j >> 5;
+#pragma unroll
+                    for (uint32_t e = 0; e < E; ++e) {
+                        if ((e & d) == 0 && (e | d) < E) {
+                            const uint32_t e2 = e | d;
+                            const uint32_t g = wb + e * 32u + lane;
+                            if (g < np && pe_gt<NW, CAP>(x[e], x[e2], keys, rr, n, w0) == ((g & k) == 0)) {
+                                const PE t = x[e];
+                                x[e] = x[e2];
+                                x[e2] = t;
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (uint32_t e = 0; e < E; ++e) {
+                        const uint32_t g = wb + e * 32u + lane;
+                        PE y;
+                        y.c = __shfl_xor_sync(0xffffffffu, x[e].c, (int)j);
+                        y.s = __shfl_xor_sync(0xffffffffu, x[e].s, (int)j);
+                        const bool keep_min = ((lane & j) == 0) == ((g & k) == 0);
+                        if (g < np && keep_min == pe_gt<NW, CAP>(x[e], y, keys, rr, n, w0)) x[e] = y;
+                    }
                 }
             }
-            __syncthreads();
         }
     }
+}
+
+// Loads the leaf's entries (window of 64 key bits from L) into registers,
+// sorts the first np positions and writes windows and slots in order.
+template <int NW, uint32_t CAP, uint32_t E>
+__device__ __forceinline__ void psort_leaf_rows(const uint64_t* keys, uint64_t* c1, uint16_t* idx, const uint32_t* rr,
+                                                uint32_t np, uint32_t n, uint32_t L, uint32_t w0) {
+    const uint32_t lane = threadIdx.x & 31u, wb = (threadIdx.x >> 5) * 32u * E;
+    const uint32_t lw = L >> 6, ls = L & 63u;
+    PE x[E];
+#pragma unroll
+    for (uint32_t e = 0; e < E; ++e) {
+        const uint32_t g = wb + e * 32u + lane;
+        uint64_t c = ~0ull;
+        if (g < n) {
+            c = keys[(size_t)lw * CAP + g];
+            if (ls) {
+                const uint64_t nx = lw + 1u < (uint32_t)NW ? keys[(size_t)(lw + 1u) * CAP + g] : 0ull;
+                c = (c << ls) | (nx >> (64u - ls));
+            }
+        }
+        x[e] = PE{c, g};
+    }
+    psort_reg<NW, CAP, E>(x, np, c1, idx, keys, rr, n, w0);
+#pragma unroll
+    for (uint32_t e = 0; e < E; ++e) {
+        const uint32_t g = wb + e * 32u + lane;
+        if (g < np) {
+            c1[g] = x[e].c;
+            idx[g] = (uint16_t)x[e].s;
+        }
+    }
+    __syncthreads();
 }
 
 // One leaf: records src[0 .. n) (or base + t when src is null), n at most
@@ -399,26 +490,16 @@ __device__ void pleaf(const PCtx<WP, MODE>& ctx, const uint32_t* src, uint32_t b
         __syncthreads();
         return;
     }
-    // window of 64 key bits from L; equal windows fall back to the words
-    // from (L + 64) / 64 on (earlier bits are the window's or shared)
+    // sort by the window of 64 key bits from L; equal windows fall back to
+    // the words from (L + 64) / 64 on (earlier bits are the window's or
+    // shared)
     const uint32_t w0 = (L + 64u) >> 6;
-    const uint32_t lw = L >> 6, ls = L & 63u;
     uint32_t npow = 32;
     while (npow < n) npow <<= 1;
-    for (uint32_t t = tid; t < npow; t += kPThreads) {
-        uint64_t c = ~0ull;
-        if (t < n) {
-            c = keys[(size_t)lw * CAP + t];
-            if (ls) {
-                const uint64_t nx = lw + 1u < (uint32_t)NW ? keys[(size_t)(lw + 1u) * CAP + t] : 0ull;
-                c = (c << ls) | (nx >> (64u - ls));
-            }
-        }
-        c1[t] = c;
-        idx[t] = (uint16_t)t;
-    }
-    __syncthreads();
-    psort_leaf<NW, CAP>(keys, c1, idx, rr, npow, n, w0);
+    if (npow <= (uint32_t)kPThreads) psort_leaf_rows<NW, CAP, 1>(keys, c1, idx, rr, npow, n, L, w0);
+    else if (npow <= 2u * kPThreads || CAP <= 2u * kPThreads)
+        psort_leaf_rows<NW, CAP, (CAP > (uint32_t)kPThreads ? 2u : 1u)>(keys, c1, idx, rr, npow, n, L, w0);
+    else psort_leaf_rows<NW, CAP, (CAP > 2u * kPThreads ? 4u : 1u)>(keys, c1, idx, rr, npow, n, L, w0);
     for (uint32_t t = tid; t < n; t += kPThreads)
         hd[t] = (t == 0 || pleaf_cmp<NW, CAP>(keys, c1, idx, t - 1u, t, n, w0) != 0) ? 1 : 0;
     __syncthreads();
