@@ -425,8 +425,11 @@ def measure_batched(paulib, stream, flush, reps, problems=4096):
     products = int(sum(a.m * b.m for a, b in pairs))
     res = {"problems": problems, "products": products, "n_qubits": pairs[0][0].n,
            "generation_s": gen_s}
-    for prec in ("fp32_fp64merge", "fp64"):
+    res["method"] = "persistent kernel (one launch); general pipeline timed beside it"
+    for prec, general in (("fp32_fp64merge", 0), ("fp64", 0), ("fp32_fp64merge", 1)):
+        paulib.set_debug(3, general)  # plans made now take the general pipeline when set
         plan = paulib.BatchPlan(As, Bs, prec, stream=stream)
+        paulib.set_debug(3, 0)
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         g = torch.cuda.CUDAGraph()
@@ -449,8 +452,8 @@ def measure_batched(paulib, stream, flush, reps, problems=4096):
             ts.append(e0.elapsed_time(e1))
         ms = statistics.mean(ts)
         outs = plan.outputs(stream=cur)
-        res["graph_" + prec] = {"ms_per_step": ms, "value": products / (ms / 1e3),
-                                "distinct_out": int(sum(o.n_terms for o in outs))}
+        res[("general_pipeline_graph_" if general else "graph_") + prec] = {
+            "ms_per_step": ms, "value": products / (ms / 1e3), "distinct_out": int(sum(o.n_terms for o in outs))}
         del outs
         plan.close()
         del g
@@ -470,6 +473,18 @@ def measure_batched(paulib, stream, flush, reps, problems=4096):
                               "note": "one paulib_multiply per product; each call synchronises once"}
     res["speedup_vs_sequential_fp64"] = seq_ms / res["graph_fp32_fp64merge"]["ms_per_step"]
     res["speedup_fp64_graph_vs_sequential_fp64"] = seq_ms / res["graph_fp64"]["ms_per_step"]
+    res["speedup_vs_general_pipeline"] = (res["general_pipeline_graph_fp32_fp64merge"]["ms_per_step"] /
+                                          res["graph_fp32_fp64merge"]["ms_per_step"])
+    # compulsory HBM bytes: every operand term read once (16 words of key at
+    # n=500, FP32 coefficient copy, phase byte), every merged term written once
+    wp_words = 16
+    terms_in = sum(a.m + b.m for a, b in pairs)
+    bytes_io = terms_in * (8 * wp_words + 8 + 1) + res["graph_fp32_fp64merge"]["distinct_out"] * (8 * wp_words + 16 + 1)
+    peak, kind = measured_peaks()
+    bound_ms = bytes_io / (peak * 1e9) * 1e3
+    res["roofline"] = {"bound": "hbm", "compulsory_bytes": bytes_io, "hbm_bound_ms": bound_ms,
+                       "frac": bound_ms / res["graph_fp32_fp64merge"]["ms_per_step"], "peak_GBs": peak,
+                       "peak_kind": kind}
     for t in As + Bs:
         t.close()
     return res
@@ -607,6 +622,22 @@ def run_ours(args):
             if rank == 0:
                 print(json.dumps({"kernels_case": "jw_hh_n200_m6000", "distinct_out": o.n_terms}), flush=True)
             o.close()
+        return
+    if args.batched_case:
+        # small case for the persistent batched kernel's profile: 512
+        # propagation-shaped problems at n=500 (about 5.5e6 products), one
+        # plan launched twice
+        from paper_2605_25974_gb300 import workloads as wl
+        pairs = wl.batch(problems=512)
+        As = [paulib.PauliSum.from_arrays(a) for a, _ in pairs]
+        Bs = [paulib.PauliSum.from_arrays(b) for _, b in pairs]
+        plan = paulib.BatchPlan(As, Bs, "fp32_fp64merge")
+        plan.launch()
+        outs = plan.outputs()
+        if rank == 0:
+            print(json.dumps({"batched_case": "batch_n500_512", "products": int(sum(a.m * b.m for a, b in pairs)),
+                              "distinct_out": int(sum(o.n_terms for o in outs))}), flush=True)
+        plan.close()
         return
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     if args.only_propagation:
@@ -891,6 +922,8 @@ def main():
     ap.add_argument("--peaks", action="store_true", help="print the measured pipe rates and exit")
     ap.add_argument("--kernels-case", action="store_true",
                     help="run the small kernel-profiling case (raw and canonical H*H, n=200, 6,000 terms) and exit")
+    ap.add_argument("--batched-case", action="store_true",
+                    help="run the small batched-kernel profiling case (512 problems at n=500) and exit")
     ap.add_argument("--method", type=int, default=-1,
                     help="canonicalisation method (0 slot sort, 1 range sort; -1: library default)")
     ap.add_argument("--coarse-factor", type=int, default=0,
