@@ -151,6 +151,26 @@ struct PCtx {
         const uint32_t ph = string_product<WP>(a, b, __ldg(ap + i), sbp[j], k);
         return rot_v(mul_v(ac[i], sbc[j]), ph);
     }
+    // Order-preserving 64-bit code of record r's key bits from position P that
+    // skips
+    // zero 64-bit windows: with v_j the window of bits [P + 64j, P + 64j + 64),
+    // K windows, j1 the first nonzero one and F = K - j1 (0 when every window
+    // is zero), the code is F in the top 6 bits and the top 58 bits of v_j1.
+    // For keys equal before P, a larger code means a larger or equal key: at
+    // the first window where two keys differ either one of them is zero there
+    // (its F is smaller) or both are nonzero at the same index.  Keys that are
+    // zero in many windows get codes spread like their first nonzero windows.
+    // Only the windows up to the first nonzero one are read.
+    __device__ __forceinline__ uint64_t skip(uint32_t r, uint32_t P) const {
+        constexpr uint32_t end = 64u * NW;
+        if (P >= end) return 0ull;
+        const uint32_t K = (end - P + 63u) >> 6;
+        for (uint32_t j = 0; j < K; ++j) {
+            const uint64_t v = window(r, P + 64u * j);
+            if (v) return ((uint64_t)(K - j) << 58) | (v >> 6);
+        }
+        return 0ull;
+    }
     // Key bits [P, P + 64) of record r (zero beyond the key), from the two
     // words that hold them.
     __device__ __forceinline__ uint64_t window(uint32_t r, uint32_t P) const {
@@ -234,26 +254,6 @@ __device__ __forceinline__ void pemit(const OutDesc& o, uint32_t pos, const uint
     o.pbase[pos] = (uint8_t)normal_phase<WP>(k, 0u);
 }
 
-// Order-preserving 64-bit code of the key bits from position P that skips
-// zero 64-bit windows: with v_j the window of bits [P + 64j, P + 64j + 64),
-// K windows, j1 the first nonzero one and F = K - j1 (0 when every window
-// is zero), the code is F in the top 6 bits and the top 58 bits of v_j1.
-// For keys equal before P, a larger code means a larger or equal key: at
-// the first window where two keys differ either one of them is zero there
-// (its F is smaller) or both are nonzero at the same index.  Keys that are
-// zero in many windows get codes spread like their first nonzero windows.
-template <int NW>
-__device__ __forceinline__ uint64_t skip_code(const uint64_t (&k)[NW], uint32_t P) {
-    constexpr uint32_t end = 64u * NW;
-    if (P >= end) return 0ull;
-    const uint32_t K = (end - P + 63u) >> 6;
-    for (uint32_t j = 0; j < K; ++j) {
-        const uint64_t v = reg_bits64<NW>(k, P + 64u * j);
-        if (v) return ((uint64_t)(K - j) << 58) | (v >> 6);
-    }
-    return 0ull;
-}
-
 // Bitonic sort of npow shared 64-bit values (a split's sample).
 __device__ __forceinline__ void psort_codes(uint64_t* c, uint32_t npow) {
     for (uint32_t k = 2; k <= npow; k <<= 1) {
@@ -274,6 +274,7 @@ __device__ __forceinline__ void psort_codes(uint64_t* c, uint32_t npow) {
 
 // Exclusive scan of the head flags over positions [0, n) in blocked chunks;
 // writes each position's run rank to seg and returns the number of runs.
+// Ends with a barrier: callers read ranks written by other threads.
 __device__ __forceinline__ uint32_t prank_heads(const uint8_t* hd, uint16_t* seg, uint32_t n, uint32_t* s_warp) {
     const uint32_t per = (n + kPThreads - 1) / kPThreads;
     const uint32_t q0 = threadIdx.x * per;
@@ -285,6 +286,7 @@ __device__ __forceinline__ uint32_t prank_heads(const uint8_t* hd, uint16_t* seg
         ex += hd[q];
         seg[q] = (uint16_t)(ex - 1u);
     }
+    __syncthreads();
     return tot;
 }
 
@@ -551,11 +553,7 @@ __device__ bool psplit(const PCtx<WP, MODE>& ctx, const uint32_t* src, uint32_t 
                 r[u] = t < kPSample ? (src ? src[pos] : base + pos) : 0u;
             }
 #pragma unroll
-            for (int u = 0; u < kPU; ++u) {
-                uint64_t k[NW];
-                ctx.key(r[u], k);
-                c[u] = skip_code<NW>(k, D);
-            }
+            for (int u = 0; u < kPU; ++u) c[u] = ctx.skip(r[u], D);
 #pragma unroll
             for (int u = 0; u < kPU; ++u) {
                 const uint32_t t = t0 + (uint32_t)u * kPThreads;
@@ -588,13 +586,7 @@ __device__ bool psplit(const PCtx<WP, MODE>& ctx, const uint32_t* src, uint32_t 
         }
 #pragma unroll
         for (int u = 0; u < kPU; ++u) {
-            if (digits) {
-                c[u] = ctx.window(r[u], D);
-            } else {
-                uint64_t k[NW];
-                ctx.key(r[u], k);
-                c[u] = skip_code<NW>(k, D);
-            }
+            c[u] = digits ? ctx.window(r[u], D) : ctx.skip(r[u], D);
         }
 #pragma unroll
         for (int u = 0; u < kPU; ++u) {
