@@ -190,13 +190,15 @@ struct PCtx {
 };
 
 // First set position >= P of a shared mask (word 0's top bit is position
-// 0), or 64 * NW when there is none.
+// 0), or 64 * NW when there is none; with `and_` given, of the mask
+// m ^ and_ (the OR and AND of a set of keys: where some of them differ).
 template <int NW>
-__device__ __forceinline__ uint32_t pmask_first(const unsigned long long* m, uint32_t P = 0) {
+__device__ __forceinline__ uint32_t pmask_first(const unsigned long long* m, uint32_t P = 0,
+                                                const unsigned long long* and_ = nullptr) {
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
         if (64u * w + 63u < P) continue;
-        uint64_t v = m[w];
+        uint64_t v = and_ ? (m[w] ^ and_[w]) : m[w];
         if (P > 64u * w) v &= ~0ull >> (P - 64u * w);
         if (v) return 64u * w + (uint32_t)__clzll((long long)v);
     }
@@ -476,8 +478,7 @@ __device__ void pleaf(const PCtx<WP, MODE>& ctx, const uint32_t* src, uint32_t b
         pmask_reduce<NW>(mo, ma, sh.mask, sh.mand);
     }
     __syncthreads();
-    pmask_finish<NW>(sh.mask, sh.mand);
-    const uint32_t L = pmask_first<NW>(sh.mask);
+    const uint32_t L = pmask_first<NW>(sh.mask, 0u, sh.mand);
     if (L >= 64u * NW) {  // one key: sum every contribution
         Acc<MODE> a;
         for (uint32_t t = tid; t < n; t += kPThreads) a.add(val[t]);
@@ -709,8 +710,7 @@ __device__ void pbig(const PCtx<WP, MODE>& ctx, const uint32_t* src, uint32_t ba
         pmask_reduce<NW>(mo, ma, sh.mask, sh.mand);
     }
     __syncthreads();
-    pmask_finish<NW>(sh.mask, sh.mand);
-    const uint32_t D = pmask_first<NW>(sh.mask);
+    const uint32_t D = pmask_first<NW>(sh.mask, 0u, sh.mand);
     if (D < 64u * NW) {
         if (sh.depth >= persist_depth<NW>()) {  // cannot happen: the depth is bounded
             if (tid == 0) atomicOr(err, ERR_STACK);
