@@ -251,6 +251,18 @@ paulib_status paulib_set_tuning(int32_t key_words, int32_t coarse_factor, int32_
  * a setting and 0 restores its default.  Applies to keys of `key_words`
  * words (0 = every size).
  * Errors: INVALID_ARG for values outside these ranges.                      */
+/* Sizes of the persistent batched kernel (paulib_multiply_batched and
+ * batch plans made afterwards; no counterpart in the paper, results never
+ * depend on them):
+ *   leaf_cap: records a CTA sorts in shared memory at once (32..2048; at
+ *       most the compiled capacity, 1,024 records up to 8-word keys, 512 for
+ *       16-word, 256 for 32-word keys; 0 = that capacity);
+ *   split_fan: a problem or range larger than a leaf is split into about
+ *       split_fan x n / leaf_cap children (1..8; 0 = 2).
+ * -1 keeps a value.  A tune-file line "batch leaf_cap split_fan" sets them
+ * too.  Errors: INVALID_ARG for values out of range.                        */
+paulib_status paulib_set_batch_tuning(int32_t leaf_cap, int32_t split_fan);
+
 paulib_status paulib_set_slot_tuning(int32_t key_words, int32_t method, int32_t leaf_cap, int32_t slot_target,
                                      int32_t slot_oversample);
 

@@ -14,9 +14,11 @@ pipeline's tunables one at a time (coordinate descent from the defaults):
   sort, its mean slot size.
 
 Cases: H*H for Jordan-Wigner-shaped sums at n=100 and n=200 (4- and 8-word
-keys), and batched products shaped like Pauli-propagation steps at n=500
-(18-word keys with the problem prefix), timed as a prepared plan on the
-general pipeline.  Results never depend on these settings; only speed does.
+keys), and batched products shaped like Pauli-propagation steps at n=500,
+timed as prepared plans: on the general pipeline (18-word keys with the
+problem prefix) and on the persistent batched kernel, whose leaf capacity
+and split fan-out are swept too (written as a line "batch leaf_cap
+split_fan").  Results never depend on these settings; only speed does.
 The best setting per key width is written as lines "key_words
 coarse_factor oversample count_ctas_per_sm range_ctas_per_sm method
 leaf_cap slot_target slot_oversample", the format the library reads from
@@ -40,6 +42,8 @@ SPACE = {
 }
 DEFAULT = {"coarse_factor": 32, "oversample": 64, "count_ctas_per_sm": 8, "range_ctas_per_sm": 2,
            "method": 1, "leaf_cap": 0, "slot_target": 0, "slot_oversample": 0}
+BATCH_SPACE = {"leaf_cap": [0, 256, 512], "split_fan": [1, 2, 3, 4]}
+BATCH_DEFAULT = {"leaf_cap": 0, "split_fan": 2}
 # smaller leaves than the default make slots oversized (the multi-pass path,
 # which serialises the leaves after it): the slot sort is tuned around its
 # default leaf
@@ -162,6 +166,29 @@ def main():
         reset()
     finally:
         paulib.set_debug(3, 0)
+    # the persistent kernel's own sizes
+    best, best_t = dict(BATCH_DEFAULT), None
+    run, reset = batch_case(As, Bs)
+
+    def measure(cfg):
+        paulib.set_batch_tuning(cfg["leaf_cap"], cfg["split_fan"])
+        reset()
+        return _timed(run, args.reps)
+    best_t = measure(best)
+    print("persistent batched kernel default %.3f ms" % best_t)
+    for name, values in BATCH_SPACE.items():
+        for v in values:
+            if v == best[name]:
+                continue
+            cfg = dict(best, **{name: v})
+            t = measure(cfg)
+            print("  %s=%d: %.3f ms" % (name, v, t))
+            if t < best_t * 0.98:
+                best, best_t = cfg, t
+    reset()
+    paulib.set_batch_tuning(best["leaf_cap"], best["split_fan"])
+    print("persistent batched kernel best %s %.3f ms" % (best, best_t))
+    lines.append("batch %d %d" % (best["leaf_cap"], best["split_fan"]))
     for s in As + Bs:
         s.close()
     with open(args.out, "w") as f:

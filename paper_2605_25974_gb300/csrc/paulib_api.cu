@@ -323,6 +323,11 @@ void load_tune_file_locked() {
         Tuning t{0, 0, 0, 0};
         SlotTuning st;
         if (line[0] == '#') continue;
+        BatchTuning bt;
+        if (std::sscanf(line, "batch %d %d", &bt.leaf_cap, &bt.split_fan) == 2) {
+            set_batch_tuning(bt);
+            continue;
+        }
         const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d %d", &kw, &t.coarse_factor, &t.oversample,
                                     &t.count_ctas_per_sm, &t.range_ctas_per_sm, &st.method, &st.leaf_cap,
                                     &st.target, &st.oversample);
@@ -354,6 +359,25 @@ std::vector<std::pair<int, SlotTuning>> g_slot_by_words;
 thread_local int g_canon_method = -1;
 thread_local int g_canon_bits = 0;
 }  // namespace
+
+namespace {
+std::mutex g_batch_mu;
+BatchTuning g_batch;
+}  // namespace
+
+BatchTuning batch_tuning() {
+    {
+        std::lock_guard<std::mutex> lt(g_tune_mu);  // the tune file may set it
+        load_tune_file_locked();
+    }
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    return g_batch;
+}
+
+void set_batch_tuning(const BatchTuning& t) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    g_batch = t;
+}
 
 SlotTuning slot_tuning_for(int key_words) {
     {
@@ -870,6 +894,19 @@ paulib_status paulib_set_tuning(int32_t key_words, int32_t coarse_factor, int32_
                                 int32_t count_ctas_per_sm, int32_t range_ctas_per_sm) {
     PAULIB_API_BEGIN
     set_tuning(key_words, Tuning{coarse_factor, oversample, count_ctas_per_sm, range_ctas_per_sm});
+    return PAULIB_OK;
+    PAULIB_API_END
+}
+
+paulib_status paulib_set_batch_tuning(int32_t leaf_cap, int32_t split_fan) {
+    PAULIB_API_BEGIN
+    if (leaf_cap < -1 || (leaf_cap > 0 && (leaf_cap < 32 || leaf_cap > 2048)))
+        fail(PAULIB_ERR_INVALID_ARG, "leaf_cap must be -1, 0 or 32..2048");
+    if (split_fan < -1 || split_fan > 8) fail(PAULIB_ERR_INVALID_ARG, "split_fan must be -1..8");
+    BatchTuning t = batch_tuning();
+    if (leaf_cap >= 0) t.leaf_cap = leaf_cap;
+    if (split_fan >= 0) t.split_fan = split_fan;
+    set_batch_tuning(t);
     return PAULIB_OK;
     PAULIB_API_END
 }

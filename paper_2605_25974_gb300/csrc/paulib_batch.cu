@@ -150,7 +150,8 @@ struct paulib_batch_plan {
     uint32_t* d_order = nullptr;  // problems by decreasing |A_b||B_b| (persistent kernel)
     uint32_t* d_ticket = nullptr;
     bool persist = false;
-    uint32_t leaf_cap = 0;  // 0: the compiled capacity
+    uint32_t leaf_cap = 0;   // 0: the compiled capacity
+    uint32_t split_fan = 0;  // 0: the kernel's default
     int ctas_per_sm = 2;
 };
 
@@ -176,7 +177,7 @@ static void persist_launch(paulib_batch_plan* p, cudaStream_t st) {
                                               bufs.as<uint32_t>(), bufs.as<uint32_t>() + p->R,
                                               reinterpret_cast<uint8_t*>(bufs.as<uint32_t>() + 2 * p->R),
                                               levels.as<PLevel>(), p->d_ticket, p->d_counts, p->d_err,
-                                              p->leaf_cap);
+                                              p->leaf_cap, p->split_fan);
     note_launch(ST_LEAF);
     check_cuda(cudaGetLastError(), "k_batch_persist");
 }
@@ -288,7 +289,9 @@ paulib_batch_plan* batch_plan_create(int32_t batch, const paulib_sum* const* a, 
         p->persist = dbg.batch_general == 0;
         for (int32_t q = 0; q < batch && p->persist; ++q)
             if ((uint64_t)b[q]->n_terms > kPNB) p->persist = false;
-        p->leaf_cap = dbg.persist_leaf > 0 ? (uint32_t)dbg.persist_leaf : 0u;
+        const BatchTuning bt = batch_tuning();
+        p->leaf_cap = dbg.persist_leaf > 0 ? (uint32_t)dbg.persist_leaf : (uint32_t)bt.leaf_cap;
+        p->split_fan = (uint32_t)bt.split_fan;
         std::vector<uint32_t> order(batch);
         for (int32_t q = 0; q < batch; ++q) order[q] = (uint32_t)q;
         std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {

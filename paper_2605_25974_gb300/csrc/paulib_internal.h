@@ -91,6 +91,17 @@ struct Tuning {
 Tuning tuning_for(int key_words);
 void set_tuning(int key_words, const Tuning& t);
 
+// Sizes of the persistent batched kernel (paulib_set_batch_tuning); never
+// change results.  leaf_cap: records of a shared-memory leaf (0: the
+// compiled capacity); split_fan: children per leaf's worth of records in a
+// sample split (0: 2).
+struct BatchTuning {
+    int leaf_cap = 0;
+    int split_fan = 0;
+};
+BatchTuning batch_tuning();
+void set_batch_tuning(const BatchTuning& t);
+
 // Test settings (paulib_set_debug); 0 = off.  hash_bits: keep only the low
 // hash_bits bits of the range sort's warp-leaf key hashes (forces the
 // hash-clash path); stack_cap: entries of a range CTA's worklist (a small cap

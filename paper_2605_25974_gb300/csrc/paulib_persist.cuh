@@ -532,8 +532,8 @@ __device__ void pleaf(const PCtx<WP, MODE>& ctx, const uint32_t* src, uint32_t b
 // leave every record in one child returns false with nothing pushed.
 template <int WP, int MODE>
 __device__ bool psplit(const PCtx<WP, MODE>& ctx, const uint32_t* src, uint32_t base, uint32_t n, uint32_t D,
-                       bool digits, uint32_t cap, uint8_t* bid, uint32_t* dst, uint32_t lo, uint32_t dbuf,
-                       PLevel* levels, unsigned char* smem, PShared<2 * WP, MODE>& sh) {
+                       bool digits, uint32_t cap, uint32_t fan, uint8_t* bid, uint32_t* dst, uint32_t lo,
+                       uint32_t dbuf, PLevel* levels, unsigned char* smem, PShared<2 * WP, MODE>& sh) {
     constexpr int NW = 2 * WP;
     using Lay = PLayout<WP, MODE>;
     uint64_t* samp = reinterpret_cast<uint64_t*>(smem + Lay::KEYS);
@@ -541,8 +541,8 @@ __device__ bool psplit(const PCtx<WP, MODE>& ctx, const uint32_t* src, uint32_t 
     const uint32_t tid = threadIdx.x;
     uint32_t nspl = kPFan - 1u;
     if (!digits) {
-        // about 2n/cap children: half a leaf each on average
-        const uint64_t want = ((uint64_t)2 * n + cap - 1) / cap;
+        // about fan * n / cap children: a fan-th of a leaf each on average
+        const uint64_t want = ((uint64_t)fan * n + cap - 1) / cap;
         nspl = (uint32_t)(want < 2 ? 2 : (want > kPFan ? kPFan : want)) - 1u;
         for (uint32_t t0 = tid; t0 < kPSample; t0 += kPU * kPThreads) {
             uint32_t r[kPU];
@@ -679,12 +679,12 @@ __device__ bool psplit(const PCtx<WP, MODE>& ctx, const uint32_t* src, uint32_t 
 // its keys are equal.
 template <int WP, int MODE>
 __device__ void pbig(const PCtx<WP, MODE>& ctx, const uint32_t* src, uint32_t base, uint32_t n, uint32_t Dhint,
-                     uint32_t cap, uint8_t* bid, uint32_t* dst, uint32_t lo, uint32_t dbuf, PLevel* levels,
+                     uint32_t cap, uint32_t fan, uint8_t* bid, uint32_t* dst, uint32_t lo, uint32_t dbuf, PLevel* levels,
                      unsigned char* smem, PShared<2 * WP, MODE>& sh, const OutDesc& o, int32_t* err) {
     constexpr int NW = 2 * WP;
     const uint32_t tid = threadIdx.x;
     if (sh.depth < kPSampleDepth &&
-        psplit<WP, MODE>(ctx, src, base, n, Dhint, false, cap, bid, dst, lo, dbuf, levels, smem, sh))
+        psplit<WP, MODE>(ctx, src, base, n, Dhint, false, cap, fan, bid, dst, lo, dbuf, levels, smem, sh))
         return;
     if (tid < (uint32_t)NW) {
         sh.mask[tid] = 0ull;
@@ -717,7 +717,7 @@ __device__ void pbig(const PCtx<WP, MODE>& ctx, const uint32_t* src, uint32_t ba
             __syncthreads();
             return;
         }
-        psplit<WP, MODE>(ctx, src, base, n, D, true, cap, bid, dst, lo, dbuf, levels, smem, sh);
+        psplit<WP, MODE>(ctx, src, base, n, D, true, cap, fan, bid, dst, lo, dbuf, levels, smem, sh);
         return;
     }
     Acc<MODE> a;
@@ -740,7 +740,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
     k_batch_persist(const ProbDesc* __restrict__ probs, const OutDesc* __restrict__ outs,
                     const uint32_t* __restrict__ order, const uint32_t* __restrict__ r0s, uint32_t nprob,
                     uint32_t* buf0, uint32_t* buf1, uint8_t* bid_all, PLevel* level_store, uint32_t* ticket,
-                    unsigned long long* counts, int32_t* err, uint32_t cap) {
+                    unsigned long long* counts, int32_t* err, uint32_t cap, uint32_t fan) {
     constexpr int NW = 2 * WP;
     using Lay = PLayout<WP, MODE>;
     using V = typename ValT<MODE>::T;
@@ -752,6 +752,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
     PLevel* levels = level_store + (size_t)blockIdx.x * persist_depth<NW>();
     const uint32_t tid = threadIdx.x;
     cap = (cap == 0 || cap > Lay::CAP) ? Lay::CAP : cap;
+    fan = fan == 0 ? 2u : fan;
 
     for (;;) {
         if (tid == 0) sh.prob = atomicAdd(ticket, 1u);
@@ -841,7 +842,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
             }
             __syncthreads();
             const uint32_t D = pmask_first<NW>(sh.mask);
-            pbig<WP, MODE>(ctx, nullptr, 0u, P, D, cap, bid, bufs[0], 0u, 0u, levels, smem, sh, o, err);
+            pbig<WP, MODE>(ctx, nullptr, 0u, P, D, cap, fan, bid, bufs[0], 0u, 0u, levels, smem, sh, o, err);
             // depth-first walk of the children, in key order
             for (;;) {
                 if (sh.depth == 0) break;
@@ -867,7 +868,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
                 if (n <= cap)
                     pleaf<WP, MODE>(ctx, bufs[cb] + lo, 0u, n, smem, sh, o);
                 else
-                    pbig<WP, MODE>(ctx, bufs[cb] + lo, 0u, n, Dh, cap, bid + lo, bufs[cb ^ 1u] + lo, lo, cb ^ 1u,
+                    pbig<WP, MODE>(ctx, bufs[cb] + lo, 0u, n, Dh, cap, fan, bid + lo, bufs[cb ^ 1u] + lo, lo, cb ^ 1u,
                                    levels, smem, sh, o, err);
             }
         }

@@ -30,7 +30,7 @@ EXPORTED = ["paulib_abi_version", "paulib_sum_create", "paulib_sum_info", "pauli
             "paulib_apply_clifford", "paulib_rotate", "paulib_multiply_pairwise",
             "paulib_group_commuting", "paulib_set_group_candidates", "paulib_set_slot_tuning",
             "paulib_last_canon_method", "paulib_sum_export_range", "paulib_last_canon_stats", "paulib_set_debug",
-            "paulib_measure_peaks"]
+            "paulib_measure_peaks", "paulib_set_batch_tuning"]
 GATES = {"h": 0, "s": 1, "cnot": 2, "cz": 3}
 STAGES = ["convert", "sample", "count", "scatter", "level2", "compact", "raw", "export", "leaf", "group", "split",
           "place"]
@@ -98,6 +98,8 @@ def load(path: Optional[str] = None):
     lib.paulib_group_commuting.restype = _i32
     lib.paulib_set_group_candidates.argtypes = [_i32]
     lib.paulib_set_group_candidates.restype = _i32
+    lib.paulib_set_batch_tuning.argtypes = [_i32, _i32]
+    lib.paulib_set_batch_tuning.restype = _i32
     lib.paulib_set_slot_tuning.argtypes = [_i32, _i32, _i32, _i32, _i32]
     lib.paulib_set_slot_tuning.restype = _i32
     lib.paulib_last_canon_method.argtypes = [ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
@@ -327,6 +329,13 @@ def set_tuning(key_words=0, coarse_factor=0, oversample=0, count_ctas_per_sm=0, 
     """Pipeline tuning for keys of ``key_words`` words (0 = all); 0 keeps a value."""
     _check(load().paulib_set_tuning(int(key_words), int(coarse_factor), int(oversample), int(count_ctas_per_sm),
                                     int(range_ctas_per_sm)))
+
+
+def set_batch_tuning(leaf_cap=-1, split_fan=-1):
+    """Sizes of the persistent batched kernel for plans made afterwards:
+    leaf capacity (0 = compiled) and split fan-out (0 = 2); -1 keeps a
+    value.  Results never depend on them."""
+    _check(load().paulib_set_batch_tuning(int(leaf_cap), int(split_fan)))
 
 
 def set_slot_tuning(key_words=0, method=-1, leaf_cap=-1, slot_target=-1, slot_oversample=-1):

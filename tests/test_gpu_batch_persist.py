@@ -232,6 +232,22 @@ def test_plan_graph_replay_on_the_persistent_kernel(lib, oracle):
         t.close()
 
 
+@pytest.mark.parametrize("leaf_cap,split_fan", [(256, 1), (0, 4), (512, 3)])
+def test_batch_tuning_sizes(lib, oracle, leaf_cap, split_fan):
+    # the autotuner's sizes for the persistent kernel: other leaf capacities
+    # and split fan-outs give the same sums
+    from paper_2605_25974_gb300 import workloads as wl
+    probs = wl.batch(problems=12, seed=680, amax=9000)
+    lib.set_batch_tuning(leaf_cap, split_fan)
+    try:
+        check_batch(lib, oracle, probs)
+    finally:
+        lib.set_batch_tuning(0, 0)
+    for bad in ((31, 2), (4096, 2), (0, 9), (-2, 0)):
+        with pytest.raises(lib.PaulibError, match="INVALID_ARG"):
+            lib.set_batch_tuning(*bad)
+
+
 def test_batch_knob_argument_checks(lib):
     for knob, value in ((3, 2), (3, -1), (4, 31), (4, 4096), (4, -5)):
         with pytest.raises(lib.PaulibError, match="INVALID_ARG"):
