@@ -151,16 +151,16 @@ struct PCtx {
         const uint32_t ph = string_product<WP>(a, b, __ldg(ap + i), sbp[j], k);
         return rot_v(mul_v(ac[i], sbc[j]), ph);
     }
-    // Order-preserving 64-bit code of record r's key bits from position P that
-    // skips
-    // zero 64-bit windows: with v_j the window of bits [P + 64j, P + 64j + 64),
-    // K windows, j1 the first nonzero one and F = K - j1 (0 when every window
-    // is zero), the code is F in the top 6 bits and the top 58 bits of v_j1.
-    // For keys equal before P, a larger code means a larger or equal key: at
-    // the first window where two keys differ either one of them is zero there
-    // (its F is smaller) or both are nonzero at the same index.  Keys that are
-    // zero in many windows get codes spread like their first nonzero windows.
-    // Only the windows up to the first nonzero one are read.
+    // Skip-zero code: an order-preserving 64-bit code of record r's key bits
+    // from position P that skips zero 64-bit windows.  With v_j the window of
+    // bits [P + 64j, P + 64j + 64), K windows, j1 the first nonzero one and
+    // F = K - j1 (0 when every window is zero), the code is F in the top 6
+    // bits and the top 58 bits of v_j1.  For keys equal before P, a larger
+    // code means a larger or equal key: at the first window where two keys
+    // differ either one of them is zero there (its F is smaller) or both are
+    // nonzero at the same index.  Keys that are zero in many windows get codes
+    // spread like their first nonzero windows.  Only the windows up to the
+    // first nonzero one are read.
     __device__ __forceinline__ uint64_t skip(uint32_t r, uint32_t P) const {
         constexpr uint32_t end = 64u * NW;
         if (P >= end) return 0ull;
@@ -526,8 +526,8 @@ __device__ void pleaf(const PCtx<WP, MODE>& ctx, const uint32_t* src, uint32_t b
 
 // Splits records src[0 .. n) (or base + t), whose keys agree before position
 // D, into key ranges: by splitters taken from a sorted sample of their
-// skip_code from D (digits false) or by the kPDigitBits key bits at D
-// (digits true).  Each record's child goes to bid[t]; the records, grouped
+// skip-zero codes (PCtx::skip) from D (digits false) or by the kPDigitBits
+// key bits at D (digits true).  Each record's child goes to bid[t]; the records, grouped
 // by child, to dst[0 .. n); the level is pushed.  A sample split that would
 // leave every record in one child returns false with nothing pushed.
 template <int WP, int MODE>
