@@ -140,7 +140,8 @@ def test_stream_full_size_single_strings(lib, oracle):
 def test_batched_full_size_graph_replay(lib, oracle):
     # the batching workload at full size (4,096 problems), as a prepared plan
     # replayed from a CUDA graph with FP32 products and FP64 merge; sampled
-    # problems compared element by element
+    # problems compared element by element with the oracle, every problem
+    # checked for key order
     import torch
     from paper_2605_25974_gb300 import workloads as wl
     probs = wl.batch(problems=4096)
@@ -166,6 +167,25 @@ def test_batched_full_size_graph_replay(lib, oracle):
         err = np.maximum(np.abs(c.real - oc.real), np.abs(c.imag - oc.imag))
         assert (err <= tol * oabs).all(), "problem %d: %.3g" % (q, float(np.max(err / oabs)))
     assert all(o.n_terms <= a.m * b.m for o, (a, b) in zip(outs, probs))
+    # every problem's output, not only the sampled ones: keys strictly
+    # increasing (a canonical sum holds each string once, in key order), and
+    # for the problems of at most 4,096 products the keys equal the distinct
+    # products a_i XOR b_j sorted (numpy's row order is the key order: x
+    # words, then z words, word 0 most significant)
+    for q, o in enumerate(outs):
+        x, z, c, _ = o.export()
+        K = np.concatenate([x, z], axis=0).T
+        if len(K) > 1:
+            D = K[1:] != K[:-1]
+            first = np.argmax(D, axis=1)
+            rows = np.arange(len(K) - 1)
+            assert D.any(axis=1).all() and (K[1:][rows, first] > K[:-1][rows, first]).all(), "problem %d" % q
+        a, b = probs[q]
+        if a.m * b.m <= 4096:
+            ka = np.concatenate([a.x, a.z], axis=0).T
+            kb = np.concatenate([b.x, b.z], axis=0).T
+            prod = np.unique((ka[:, None, :] ^ kb[None, :, :]).reshape(-1, ka.shape[1]), axis=0)
+            assert np.array_equal(K, prod), "problem %d" % q
     plan.close()
     for t in As + Bs:
         t.close()
