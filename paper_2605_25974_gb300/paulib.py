@@ -368,8 +368,10 @@ def measure_peaks(stream=None):
 
 def set_debug(knob, value):
     """Test settings: knob 1 = warp-leaf hash bits kept (forces the hash-clash
-    path), knob 2 = range-CTA worklist capacity (forces the stack error);
-    value 0 turns a setting off."""
+    path), knob 2 = range-CTA worklist capacity (forces the stack error),
+    knob 3 = 1: batch plans made afterwards take the general pipeline,
+    knob 4 = the persistent batched kernel's leaf capacity (forces its
+    splits on small inputs); value 0 turns a setting off."""
     _check(load().paulib_set_debug(int(knob), int(value)))
 
 
