@@ -35,7 +35,7 @@ constexpr int kPThreads = 256;                  // threads of a persistent CTA
 constexpr uint32_t kPNB = 64;                   // most terms of a right operand
 constexpr uint32_t kPDigitBits = 8;             // key bits of a digit split
 constexpr uint32_t kPFan = 1u << kPDigitBits;   // most children of a split
-constexpr uint32_t kPSample = 1024;             // sampled codes per sample split
+constexpr uint32_t kPSample = 1024;             // most sampled codes per sample split
 constexpr uint32_t kPSampleDepth = 6;           // levels that may split by sample
 constexpr int kPU = 4;                          // records per thread in flight
 static_assert(kPFan == (uint32_t)kPThreads, "one child per thread");
@@ -544,32 +544,35 @@ __device__ bool psplit(const PCtx<WP, MODE>& ctx, const uint32_t* src, uint32_t 
         // about fan * n / cap children: a fan-th of a leaf each on average
         const uint64_t want = ((uint64_t)fan * n + cap - 1) / cap;
         nspl = (uint32_t)(want < 2 ? 2 : (want > kPFan ? kPFan : want)) - 1u;
-        for (uint32_t t0 = tid; t0 < kPSample; t0 += kPU * kPThreads) {
+        // about 16 sampled codes per child (64 .. kPSample, a power of two)
+        uint32_t S = 64;
+        while (S < 16u * (nspl + 1u) && S < kPSample) S <<= 1;
+        for (uint32_t t0 = tid; t0 < S; t0 += kPU * kPThreads) {
             uint32_t r[kPU];
             uint64_t c[kPU];
 #pragma unroll
             for (int u = 0; u < kPU; ++u) {
                 const uint32_t t = t0 + (uint32_t)u * kPThreads;
-                const uint32_t pos = (uint32_t)(((uint64_t)t * n) / kPSample);
-                r[u] = t < kPSample ? (src ? src[pos] : base + pos) : 0u;
+                const uint32_t pos = (uint32_t)(((uint64_t)t * n) / S);
+                r[u] = t < S ? (src ? src[pos] : base + pos) : 0u;
             }
 #pragma unroll
             for (int u = 0; u < kPU; ++u) c[u] = ctx.skip(r[u], D);
 #pragma unroll
             for (int u = 0; u < kPU; ++u) {
                 const uint32_t t = t0 + (uint32_t)u * kPThreads;
-                if (t < kPSample) samp[t] = c[u];
+                if (t < S) samp[t] = c[u];
             }
         }
         __syncthreads();
-        psort_codes(samp, kPSample);
+        psort_codes(samp, S);
         // A code repeated among the splitters is frequent: its last copy
         // becomes its successor, so that the code gets a child of its own.
         uint64_t c = 0ull;
         if (tid < nspl) {
-            c = samp[((uint64_t)(tid + 1u) * kPSample) / (nspl + 1u)];
-            const bool dup = tid > 0 && samp[((uint64_t)tid * kPSample) / (nspl + 1u)] == c;
-            const bool last = tid + 1u == nspl || samp[((uint64_t)(tid + 2u) * kPSample) / (nspl + 1u)] != c;
+            c = samp[((uint64_t)(tid + 1u) * S) / (nspl + 1u)];
+            const bool dup = tid > 0 && samp[((uint64_t)tid * S) / (nspl + 1u)] == c;
+            const bool last = tid + 1u == nspl || samp[((uint64_t)(tid + 2u) * S) / (nspl + 1u)] != c;
             if (dup && last && c != ~0ull) c += 1ull;
         }
         __syncthreads();
